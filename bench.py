@@ -1,0 +1,372 @@
+#!/usr/bin/env python
+"""Adam iterations per second of the deep-FBSDE training step on GB300.
+
+One step = one pass of the whole hot path on one batch: Philox increments and
+Euler-Maruyama paths for M paths x N steps, the network and Z = grad_x u at
+every point, the loss and its Theta-gradient (tangent + adjoint sweeps and
+weight-gradient contractions), and the Adam update.  The default workload is
+100-D Black-Scholes-Barenblatt with M = 4096 paths, N = 64 steps and a ResNet
+of 5 blocks x 256 tanh, in the BF16 tensor-core form, with the FP32 CUDA-core
+form timed beside it.
+
+    python bench.py [--gpus N] [--steps K] [--warmup W] [--impl ours|reference]
+
+Under torchrun each rank runs an independent replica (its own seed) of the
+workload; the job value is all ranks' steps / the slowest rank's time.
+"""
+from __future__ import annotations
+
+import argparse
+import hashlib
+import json
+import os
+import statistics
+import subprocess
+import sys
+import threading
+import time
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+if ROOT not in sys.path:
+    sys.path.insert(0, ROOT)
+
+METRIC = "Adam iters/sec, 100-D BSB M=4096 N=64, BF16 vs FP32 form at Y0 rel err ≤1%"
+DEFAULT_WORKLOAD = "bsb_d100_n64_m4096_resnet5x256_tanh"
+
+
+def parse_args():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=200)
+    ap.add_argument("--warmup", type=int, default=10)
+    ap.add_argument("--impl", choices=["ours", "reference"], default="ours")
+    ap.add_argument("--form", choices=["bf16", "fp32"], default="bf16")
+    ap.add_argument("--workload", default=DEFAULT_WORKLOAD)
+    ap.add_argument("--fp32-steps", type=int, default=10,
+                    help="timed steps of the FP32 form beside a BF16 run (0: skip)")
+    ap.add_argument("--accuracy-steps", type=int, default=5000,
+                    help="Adam steps of the accuracy run (0: skip)")
+    ap.add_argument("--cpu-sample-paths", type=int, default=256)
+    ap.add_argument("--cpu-iters", type=int, default=3)
+    ap.add_argument("--no-cpu-baseline", action="store_true")
+    return ap.parse_args()
+
+
+# ----------------------------------------------------------------- clocks
+
+class ClockSampler:
+    """nvidia-smi samples of SM clock and throttle reasons during the timed region."""
+    FIELDS = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
+              "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
+              "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, gpu_id: str):
+        self.gpu_id, self.rows, self.proc = gpu_id, [], None
+
+    def start(self):
+        try:
+            cmd = ["nvidia-smi", f"--query-gpu={self.FIELDS}", "--format=csv,noheader,nounits",
+                   "-lms", "100"]
+            if self.gpu_id:
+                cmd += ["-i", self.gpu_id]
+            self.proc = subprocess.Popen(cmd, stdout=subprocess.PIPE, stderr=subprocess.DEVNULL, text=True)
+            self.thread = threading.Thread(target=self._read, daemon=True)
+            self.thread.start()
+        except Exception:
+            self.proc = None
+
+    def _read(self):
+        for line in self.proc.stdout:
+            parts = [p.strip() for p in line.split(",")]
+            if len(parts) >= 9:
+                self.rows.append(parts)
+
+    def stop(self):
+        if self.proc is None:
+            return {"sm_mhz": None, "sm_max_mhz": None, "reasons": ["nvidia-smi unavailable"]}
+        time.sleep(0.25)
+        self.proc.terminate()
+        try:
+            self.proc.wait(timeout=5)
+        except Exception:
+            self.proc.kill()
+        self.thread.join(timeout=2)
+        sm = [float(r[1]) for r in self.rows if r[1].replace(".", "").isdigit()]
+        smax = [float(r[2]) for r in self.rows if r[2].replace(".", "").isdigit()]
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        reasons = sorted({names[k] for r in self.rows for k in range(4) if r[5 + k].lower() == "active"})
+        return {"sm_mhz": statistics.median(sm) if sm else None,
+                "sm_max_mhz": max(smax) if smax else None, "reasons": reasons,
+                "samples": len(self.rows)}
+
+
+def gpu_id_of(dev_index: int) -> str:
+    import torch
+    try:
+        p = torch.cuda.get_device_properties(dev_index)
+        return "%08X:%02X:%02X.0" % (p.pci_domain_id, p.pci_bus_id, p.pci_device_id)
+    except Exception:
+        return ""
+
+
+# ----------------------------------------------------------------- peaks / traffic
+
+def measured_peaks():
+    path = os.path.join(ROOT, "MEASURED_PEAKS.json")
+    if os.path.exists(path):
+        with open(path) as f:
+            d = json.load(f)
+        return d, "measured"
+    return {"hbm_gbs": 6800.0, "bf16_tflops": 1900.0, "bf16_tflops_sustained": 1700.0,
+            "sm_max_mhz": 2070.0}, "fallback"
+
+
+def source_hash() -> str:
+    h = hashlib.sha256()
+    csrc = os.path.join(ROOT, "paper_1910_11623_gb300", "csrc")
+    for f in sorted(os.listdir(csrc)):
+        with open(os.path.join(csrc, f), "rb") as fh:
+            h.update(f.encode() + fh.read())
+    return h.hexdigest()[:16]
+
+
+def ncu_traffic(form: str, workload: str):
+    """DRAM bytes per launch of the dominant kernel from a committed ncu
+    summary, or None when none exists for the current sources."""
+    path = os.path.join(ROOT, "profiles", f"traffic_{form}_{workload}.json")
+    if not os.path.exists(path):
+        return None
+    with open(path) as f:
+        d = json.load(f)
+    if d.get("source_hash") != source_hash():
+        return None
+    return d.get("dram_bytes_per_launch")
+
+
+# ----------------------------------------------------------------- CPU oracle
+
+def cpu_oracle_rate(workload, sample_paths: int, iters: int):
+    """The FP64 oracle's train step on a bounded sample of the workload (the
+    first `sample_paths` paths), scaled to full-workload iterations/s."""
+    import numpy as np
+    from oracle import fbsde as F
+    from tests.helpers import oracle_specs
+    p = workload.problem
+    sample = type(p)(**{**p.__dict__, "M": sample_paths})
+    op, oa = oracle_specs(sample, workload.arch)
+    theta = F.init_params(op, oa, workload.seed)
+    m, v = np.zeros_like(theta), np.zeros_like(theta)
+    F.train_step(op, oa, theta, m, v, workload.seed, 1, workload.lr)  # warm-up
+    t0 = time.perf_counter()
+    for s in range(2, 2 + iters):
+        _, _, theta, m, v = F.train_step(op, oa, theta, m, v, workload.seed, s, workload.lr)
+    dt = (time.perf_counter() - t0) / iters
+    scale = p.M / sample_paths
+    return {"value": 1.0 / (dt * scale), "unit": "it/s", "cores": os.cpu_count(),
+            "kind": "oracle",
+            "sample": f"{iters} FP64 train steps on {sample_paths} of {p.M} paths "
+                      f"({dt:.3f} s each), scaled x{scale:g} to the full batch; "
+                      f"NumPy with its BLAS on all {os.cpu_count()} host cores"}
+
+
+def run_reference(args):
+    import paper_1910_11623_gb300 as P
+    w = P.workloads.WORKLOADS[args.workload]
+    steps = max(1, min(args.steps, 3))
+    base = cpu_oracle_rate(w, args.cpu_sample_paths, steps)
+    line = {"metric": METRIC, "value": base["value"], "unit": "it/s", "n_gpus": args.gpus,
+            "steps": steps, "warmup": 1, "ms_per_step": 1000.0 / base["value"],
+            "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f64",
+            "data": "synthetic (Philox Brownian paths, seeded Xavier init)",
+            "config": {"workload": args.workload}, "impl": "reference",
+            "cpu_baseline": base,
+            "e2e": {"value": base["value"], "unit": "it/s", "h2d_bytes_per_step": 0,
+                    "d2h_bytes_per_step": 0}}
+    print(json.dumps(line))
+
+
+# ----------------------------------------------------------------- GPU arm
+
+def time_steps(solver, theta, m, v, first_step, K, lr):
+    import torch
+    st = solver.stream
+    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    e0.record(st)
+    for s in range(first_step, first_step + K):
+        solver.train_step(theta, m, v, s, lr)
+    e1.record(st)
+    e1.synchronize()
+    return e0.elapsed_time(e1)
+
+
+def main():
+    args = parse_args()
+    world = int(os.environ.get("WORLD_SIZE", "1"))
+    rank = int(os.environ.get("RANK", "0"))
+    local = int(os.environ.get("LOCAL_RANK", "0"))
+
+    if args.impl == "reference":
+        if rank == 0:
+            run_reference(args)
+        return
+
+    import torch
+    import torch.distributed as dist
+    import paper_1910_11623_gb300 as P
+    from paper_1910_11623_gb300 import _lib as L
+
+    torch.cuda.set_device(local)
+    if world > 1:
+        dist.init_process_group("nccl", device_id=torch.device("cuda", local))
+
+    def barrier():
+        if world > 1:
+            dist.barrier()
+        torch.cuda.synchronize()
+
+    w = P.workloads.WORKLOADS[args.workload].with_prec(args.form)
+    solver = P.Solver(w.problem, w.arch, seed=w.seed + rank)
+    theta = solver.init_params()
+    m, v = torch.zeros_like(theta), torch.zeros_like(theta)
+    for s in range(1, args.warmup + 1):
+        solver.train_step(theta, m, v, s, w.lr)
+    barrier()
+
+    clocks = ClockSampler(gpu_id_of(local))
+    clocks.start()
+    L.fbsde_profile_enable(solver.ctx, True)
+    n0 = L.fbsde_launch_count(solver.ctx)
+    barrier()
+    ms = time_steps(solver, theta, m, v, args.warmup + 1, args.steps, w.lr)
+    barrier()
+    launches = L.fbsde_launch_count(solver.ctx) - n0
+    clk = clocks.stop()
+    prof = [L.fbsde_profile_read(solver.ctx, c) for c in range(3)]
+    L.fbsde_profile_enable(solver.ctx, False)
+
+    t = torch.tensor([ms], device="cuda")
+    if world > 1:
+        dist.all_reduce(t, op=dist.ReduceOp.MAX)
+    ms_max = float(t.item())
+    value = world * args.steps / (ms_max / 1000.0)
+
+    # end to end through the public API: per step, x0 from pinned host memory
+    # to the device, the training step, and the loss / Y0 back to the host.
+    D = w.problem.D
+    x0_host = torch.tensor(w.problem.x0, dtype=torch.float32).pin_memory()
+    x0_dev = torch.empty(D, device="cuda")
+    out_host = torch.empty(2, dtype=torch.float32).pin_memory()
+    out_dev = torch.empty(2, device="cuda")
+    e2e_steps = max(1, min(args.steps, 50))
+    barrier()
+    t0 = time.perf_counter()
+    first = args.warmup + args.steps + 1
+    with torch.cuda.stream(solver.stream):
+        for s in range(first, first + e2e_steps):
+            x0_dev.copy_(x0_host, non_blocking=True)
+            L.fbsde_set_x0_device(solver.ctx, x0_dev.data_ptr())
+            solver.train_step(theta, m, v, s, w.lr, out_dev[0:1], out_dev[1:2])
+            out_host.copy_(out_dev, non_blocking=True)
+            solver.stream.synchronize()
+    e2e_s = time.perf_counter() - t0
+    te = torch.tensor([e2e_s], device="cuda")
+    if world > 1:
+        dist.all_reduce(te, op=dist.ReduceOp.MAX)
+    e2e = {"value": world * e2e_steps / float(te.item()), "unit": "it/s",
+           "h2d_bytes_per_step": D * 4, "d2h_bytes_per_step": 8}
+
+    out = None
+    if rank == 0:
+        peaks, peak_src = measured_peaks()
+        dom = max(range(2), key=lambda c: prof[c][0])
+        dms, dn, dfl = prof[dom]
+        if args.form == "bf16":
+            peak = peaks["bf16_tflops_sustained"]
+            bound, unit = "tensor", "TFLOP/s"
+            achieved = dfl / (dms / 1000.0) / 1e12 if dms > 0 else None
+        else:
+            # FP32 FFMA: 152 SMs x 128 lanes x 2 flop x max SM clock
+            peak = 152 * 128 * 2 * peaks.get("sm_max_mhz", 2070.0) * 1e6 / 1e12
+            bound, unit = "alu", "TFLOP/s"
+            achieved = dfl / (dms / 1000.0) / 1e12 if dms > 0 else None
+        traffic = ncu_traffic(args.form, args.workload)
+        out = {
+            "metric": METRIC, "value": value, "unit": "it/s", "n_gpus": world,
+            "steps": args.steps, "warmup": args.warmup, "ms_per_step": ms_max / args.steps,
+            "higher_is_better": True, "scaling": "weak", "vs_baseline": None,
+            "dtype": "bf16" if args.form == "bf16" else "f32",
+            "data": "synthetic (Philox Brownian paths, seeded Xavier init)",
+            "config": {"workload": args.workload, "form": args.form, "D": w.problem.D,
+                       "N": w.problem.N, "M": w.problem.M, "arch": w.arch.kind,
+                       "width": w.arch.width, "depth": w.arch.depth, "act": w.arch.act,
+                       "parallelism": "replicas" if world > 1 else "single",
+                       "l2": "working set per step >> 126 MB L2 (no flush needed)"},
+            "roofline": {"bound": bound, "achieved": achieved, "peak": peak, "unit": unit,
+                         "frac": (achieved / peak) if achieved else None,
+                         "traffic": traffic,
+                         "kernel": ["point contractions", "weight-gradient contractions"][dom],
+                         "launches": dn, "ms_total": dms, "flops_total": dfl,
+                         "peak_source": (peak_src + (" sustained bf16" if args.form == "bf16"
+                                                     else " FP32 FFMA from SM count and max clock"))},
+            "kernel_classes": {name: {"ms": p[0], "launches": p[1], "flops": p[2]}
+                               for name, p in zip(["points", "wgrad", "other"], prof)},
+            "clocks": clk, "e2e": e2e, "gpu_launches": int(launches),
+        }
+
+    # FP32 form beside the BF16 form (same workload, same GPU)
+    if args.form == "bf16" and args.fp32_steps > 0:
+        del solver
+        torch.cuda.empty_cache()
+        w32 = w.with_prec("fp32")
+        s32 = P.Solver(w32.problem, w32.arch, seed=w.seed + rank)
+        th32 = s32.init_params()
+        m32, v32 = torch.zeros_like(th32), torch.zeros_like(th32)
+        for s in range(1, 3):
+            s32.train_step(th32, m32, v32, s, w.lr)
+        barrier()
+        ms32 = time_steps(s32, th32, m32, v32, 3, args.fp32_steps, w.lr)
+        t = torch.tensor([ms32], device="cuda")
+        if world > 1:
+            dist.all_reduce(t, op=dist.ReduceOp.MAX)
+        if out is not None:
+            v32rate = world * args.fp32_steps / (float(t.item()) / 1000.0)
+            out["fp32_form"] = {"value": v32rate, "unit": "it/s", "steps": args.fp32_steps}
+            out["speedup_vs_fp32_form"] = value / v32rate
+        del s32
+        torch.cuda.empty_cache()
+
+    # accuracy: train from Theta_0 and track |Y0 - closed form| / closed form
+    if args.accuracy_steps > 0 and out is not None and w.problem.kind == "bsb" and w.problem.D == 100:
+        target = P.workloads.BSB_Y0_D100
+        sa = P.Solver(w.problem, w.arch, seed=w.seed)
+        th = sa.init_params()
+        ma, va = torch.zeros_like(th), torch.zeros_like(th)
+        t0 = time.perf_counter()
+        t_hit, errs = None, []
+        for s in range(1, args.accuracy_steps + 1):
+            _, y0 = sa.train_step(th, ma, va, s, w.lr)
+            if s % 50 == 0 or s == args.accuracy_steps:
+                err = abs(y0.item() - target) / target
+                errs.append(err)
+                if t_hit is None and err <= 0.01:
+                    t_hit = (time.perf_counter() - t0, s)
+        _, y0 = sa.rollout_loss(th, 10**6)
+        out["accuracy"] = {"steps": args.accuracy_steps, "y0": y0.item(), "y0_closed_form": target,
+                           "y0_rel_err": abs(y0.item() - target) / target,
+                           "time_to_1pct_s": t_hit[0] if t_hit else None,
+                           "steps_to_1pct": t_hit[1] if t_hit else None,
+                           "wall_s": time.perf_counter() - t0}
+        del sa
+
+    if out is not None and not args.no_cpu_baseline:
+        out["cpu_baseline"] = cpu_oracle_rate(P.workloads.WORKLOADS[args.workload],
+                                              args.cpu_sample_paths, args.cpu_iters)
+    if rank == 0:
+        print(json.dumps(out))
+    if world > 1:
+        dist.barrier()
+        dist.destroy_process_group()
+
+
+if __name__ == "__main__":
+    main()

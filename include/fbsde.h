@@ -1,0 +1,220 @@
+/*
+ * fbsde.h -- C ABI of libfbsde, the GB300 (sm_103a) hot path of the deep
+ * FBSDE solver of Guler, Laignelet and Parpas, "Towards Robust and Stable Deep
+ * Learning Algorithms for Forward Backward Stochastic Differential Equations"
+ * (arXiv 1910.11623).
+ *
+ * What one call computes, for M sample paths over N uniform Euler steps:
+ *   - Brownian increments Delta W_n ~ N(0, Delta t) (Section 2.2, Eq. "disc
+ *     equations", first line) from a counter-based Philox4x32-10 stream;
+ *   - the forward Euler-Maruyama path X_{n+1} = X_n + sigma(X_n) Delta W_n
+ *     (Eq. "disc equations", second line; mu = 0 for every supported problem);
+ *   - Y_n = u(t_n, X_n; Theta) and Z_n = grad_x u(t_n, X_n; Theta) for one
+ *     network shared by all time points (Section 2.2), in the architectures of
+ *     Section 3.1 (fully connected, ResNet, NAIS-Net);
+ *   - the loss of Eq. "loss": the squared Y-residual
+ *     Y_{n+1} - Y_n - phi Delta t - Z_n^T sigma Delta W_n summed over paths and
+ *     steps, plus the squared terminal mismatch Y_N - g(X_N), plus (optional,
+ *     the term suggested right after Eq. "loss") |Z_N - grad g(X_N)|^2;
+ *   - its gradient in Theta, including the mixed second derivative that Z
+ *     brings in; and an Adam step (Section 4.1, learning rate 1e-3).
+ *
+ * Conventions shared by every entry point:
+ *   - Pointers named *_dev are CUDA device pointers; *_host are host pointers.
+ *     The caller owns every buffer it passes; the context owns its workspace
+ *     (allocated in fbsde_create, freed in fbsde_destroy).
+ *   - All device work is enqueued on the stream given to fbsde_create, with no
+ *     host synchronisation inside compute calls: results are ready once that
+ *     stream reaches them.
+ *   - Nothing throws across the ABI.  Every call returns an fbsde_status; on
+ *     failure a one-line reason is kept per context (fbsde_last_error).
+ *   - Parameter vector Theta: FP32, contiguous, in this order
+ *       W_in [w x (D+1)] row-major (column 0 multiplies t), b_in [w];
+ *       per layer l = 1..L:  FC / ResNet: W_l [w x w], b_l [w]
+ *                            NAIS:        R_l [w x w], C_l [w], B_l [w x (D+1)]
+ *       w_o [w], b_o [1].
+ *     NAIS uses A_l = -R_l^T R_l - eps I (Section 3.1); the context forms A_l.
+ *   - Noise: Philox4x32-10 (Salmon et al., SC'11) with key (seed mod 2^32,
+ *     seed >> 32); the increment of step n, path m, dimensions 4q..4q+3 of
+ *     iteration `iter` uses counter (q, n, m, iter mod 2^32); word pairs
+ *     (w0,w1), (w2,w3) give two Box-Muller pairs with u = (k + 1/2) 2^-32.
+ */
+#ifndef FBSDE_H
+#define FBSDE_H
+
+#include <stddef.h>
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+typedef enum {
+    FBSDE_OK = 0,
+    FBSDE_ERR_INVALID = 1,     /* bad argument or specification            */
+    FBSDE_ERR_UNSUPPORTED = 2, /* valid request this library does not serve */
+    FBSDE_ERR_CUDA = 3,        /* a CUDA runtime/driver call failed          */
+    FBSDE_ERR_NONFINITE = 4,   /* loss or gradient not finite (checked by fbsde_check_finite) */
+    FBSDE_ERR_TIMEOUT = 5,     /* a bounded device-side wait gave up         */
+    FBSDE_ERR_OOM = 6          /* device allocation failed                   */
+} fbsde_status;
+
+/* Benchmark problems of Section 4. */
+typedef enum {
+    FBSDE_BSB = 0, /* Black-Scholes-Barenblatt: sigma(x) = sigma diag(x),
+                      phi = r (y - z^T x), g(x) = ||x||^2                       */
+    FBSDE_HJB = 1  /* Hamilton-Jacobi-Bellman: sigma = sqrt(2) I, phi = ||z||^2,
+                      g(x) = ln(0.5 (1 + ||x||^2))                              */
+} fbsde_kind;
+
+/* Network architectures of Section 3.1 / Section 4.1.  Every architecture
+ * has an input lift h_0 = act(W_in (t, x) + b_in) and a linear read-out
+ * y = w_o^T h_L + b_o. */
+typedef enum {
+    FBSDE_FC = 0,     /* h_l = act(W_l h_{l-1} + b_l)                           */
+    FBSDE_RESNET = 1, /* h_l = h_{l-1} + act(W_l h_{l-1} + b_l)  (Euler, h = 1)  */
+    FBSDE_NAIS = 2    /* h_l = h_{l-1} + h act(A_l h_{l-1} + B_l (t,x) + C_l)    */
+} fbsde_arch_kind;
+
+typedef enum { FBSDE_SIN = 0, FBSDE_TANH = 1 } fbsde_act;
+
+/* Arithmetic of the network GEMMs.  FBSDE_FP32: CUDA-core FP32 throughout.
+ * FBSDE_BF16: BF16 operands on the tcgen05 tensor cores with FP32
+ * accumulation; X, Y, residuals, reductions and Adam stay FP32. */
+typedef enum { FBSDE_FP32 = 0, FBSDE_BF16 = 1 } fbsde_prec;
+
+/* Problem specification (Section 2.1 Eq. "coupled" with mu = 0, Section 4). */
+typedef struct {
+    int kind;               /* fbsde_kind                                       */
+    int D;                  /* space dimension d >= 1                           */
+    int N;                  /* Euler steps, Delta t = T / N, N >= 1             */
+    int M;                  /* paths (batch size of Eq. "loss"), M >= 1         */
+    double T;               /* horizon > 0                                      */
+    double r;               /* BSB rate r (ignored for HJB)                     */
+    double sigma;           /* BSB volatility sigma (ignored for HJB)           */
+    const double* x0_host;  /* X_0 = x0, D values, copied at create             */
+    int terminal_grad_term; /* 1: add sum_m |Z_N - grad g(X_N)|^2 to the loss   */
+} fbsde_problem;
+
+/* Architecture specification (Section 3.1). */
+typedef struct {
+    int kind;          /* fbsde_arch_kind                                       */
+    int width;         /* w, multiple of 16, 16 <= w <= 256                      */
+    int depth;         /* L hidden layers / blocks, 0 <= L <= 16                */
+    int act;           /* fbsde_act                                             */
+    double h;          /* NAIS step h > 0 (Section 3.1); ignored otherwise      */
+    double eps;        /* NAIS eps > 0 in A = -R^T R - eps I (paper: 0.01)      */
+    double proj_delta; /* NAIS bound on ||R^T R||_F; <= 0 selects 0.99 (2/h - eps) */
+    int prec;          /* fbsde_prec                                            */
+} fbsde_arch;
+
+typedef struct fbsde_ctx fbsde_ctx;
+
+/* Create a context for one problem and architecture.  Validates both specs
+ * before touching the GPU (FBSDE_ERR_INVALID on a bad value, with the reason
+ * in *err_msg_host if non-NULL: up to 255 chars + NUL), then allocates the
+ * workspace on the current CUDA device.  `cuda_stream` is a cudaStream_t
+ * (NULL = legacy default stream).  N_max >= N sizes the workspace for later
+ * fbsde_set_level calls (pass 0 for N_max = N).  On success *out owns the
+ * context. */
+fbsde_status fbsde_create(const fbsde_problem* problem, const fbsde_arch* arch,
+                          uint64_t seed, void* cuda_stream, int N_max,
+                          fbsde_ctx** out, char* err_msg_host);
+
+/* Free the workspace and the context (NULL is accepted). */
+fbsde_status fbsde_destroy(fbsde_ctx* ctx);
+
+/* Number of FP32 entries of Theta for this context's problem/architecture. */
+size_t fbsde_num_params(const fbsde_ctx* ctx);
+
+/* Number of parameters for a specification, without a context or a GPU;
+ * 0 if the specification is invalid. */
+size_t fbsde_param_count(const fbsde_problem* problem, const fbsde_arch* arch);
+
+/* Theta_0: Xavier-normal weights N(0, 2 / (fan_in + fan_out)) and zero
+ * biases; normal number i of the flat vector comes from Philox counter
+ * (i >> 2, 0, 0, 0) under key (seed_lo ^ 0x494E4954, seed_hi), Box-Muller
+ * slot i & 3.  NAIS R blocks are then projected onto ||R^T R||_F <= delta
+ * (Section 3.1).  theta_dev: fbsde_num_params floats. */
+fbsde_status fbsde_init_params(fbsde_ctx* ctx, float* theta_dev);
+
+/* Loss of Eq. "loss" and Y_0 = u(0, x0; Theta) for the paths of iteration
+ * `iter`.  theta_dev: read-only; loss_dev, y0_dev: one float each. */
+fbsde_status fbsde_rollout_loss(fbsde_ctx* ctx, const float* theta_dev, uint64_t iter,
+                                float* loss_dev, float* y0_dev);
+
+/* As fbsde_rollout_loss, plus d loss / d Theta into grad_dev (num_params
+ * floats, overwritten).  The gradient includes the mixed derivative
+ * d Z / d Theta (Section 2.2: Z by automatic differentiation). */
+fbsde_status fbsde_rollout_grad(fbsde_ctx* ctx, const float* theta_dev, uint64_t iter,
+                                float* loss_dev, float* y0_dev, float* grad_dev);
+
+/* One training iteration (Section 4.1): loss and gradient at Theta for the
+ * paths of iteration `step`, then Adam (beta1 0.9, beta2 0.999, eps 1e-8,
+ * bias-corrected, `step` >= 1 counts Adam steps) on theta_dev with moments
+ * adam_m_dev / adam_v_dev (num_params floats each, caller zeroes them before
+ * step 1), then the NAIS projection.  loss_dev / y0_dev receive the values at
+ * the Theta the step started from. */
+fbsde_status fbsde_train_step(fbsde_ctx* ctx, float* theta_dev, float* adam_m_dev,
+                              float* adam_v_dev, uint64_t step, float lr,
+                              float* loss_dev, float* y0_dev);
+
+/* Per-point detail of one evaluation, for checking and analysis:
+ * Y_dev [(N+1) * M] with index n * M + m, Z_dev [(N+1) * M * D] with index
+ * (n * M + m) * D + i, path_loss_dev [M] (the per-path terms of Eq. "loss"
+ * whose sum is the loss).  Any pointer may be NULL. */
+fbsde_status fbsde_rollout_detail(fbsde_ctx* ctx, const float* theta_dev, uint64_t iter,
+                                  float* Y_dev, float* Z_dev, float* path_loss_dev);
+
+/* The Brownian increments and paths of iteration `iter` (Eq. "disc
+ * equations"): dW_dev [N * M * D] index (n * M + m) * D + i, X_dev
+ * [(N+1) * M * D] index (n * M + m) * D + i.  Either may be NULL. */
+fbsde_status fbsde_sample_paths(fbsde_ctx* ctx, uint64_t iter, float* dW_dev, float* X_dev);
+
+/* Raw Philox4x32-10 blocks: out_dev[4 j .. 4 j + 3] = Philox(ctr_dev[4 j ..
+ * 4 j + 3], key) for j < count, key = (key0, key1).  Device pointers; the
+ * work runs on `cuda_stream`.  The generator's definition is Salmon et al.,
+ * SC'11; the paper only asks for Delta W_n ~ N(0, Delta t). */
+fbsde_status fbsde_philox4x32_10(const uint32_t* ctr_dev, uint32_t key0, uint32_t key1,
+                                 size_t count, uint32_t* out_dev, void* cuda_stream);
+
+/* Multilevel discretisation (Section 3.2): switch the context to N_level
+ * Euler steps (Delta t = T / N_level), 1 <= N_level <= N_max.  Theta and the
+ * Adam moments are untouched, so training continues on the finer grid. */
+fbsde_status fbsde_set_level(fbsde_ctx* ctx, int N_level);
+
+/* Replace the initial condition X_0 = x0 (D host doubles), e.g. for the
+ * generalisation test of Section 4.2 (perturbed X_0, same Theta). */
+fbsde_status fbsde_set_x0(fbsde_ctx* ctx, const double* x0_host);
+
+/* Waits for the context's stream and reports FBSDE_ERR_NONFINITE if the last
+ * loss or gradient produced by this context held a NaN or Inf. */
+fbsde_status fbsde_check_finite(fbsde_ctx* ctx);
+
+/* Replace x0 from a device buffer (D floats), ordered on the context stream:
+ * the variant of fbsde_set_x0 for callers that stage x0 in device memory. */
+fbsde_status fbsde_set_x0_device(fbsde_ctx* ctx, const float* x0_dev);
+
+/* Kernel-class timing.  Classes: 0 = contractions over the points (network
+ * forward, Z-reverse, tangent and adjoint sweeps), 1 = weight-gradient
+ * contractions, 2 = everything else (noise and paths, residuals and loss,
+ * reductions, Adam).  fbsde_profile_enable(ctx, 1) resets the counters and
+ * brackets every later launch with CUDA events on the context stream;
+ * fbsde_profile_read waits for the stream and returns, for class `cls`, the
+ * summed device time in ms, the number of launches and the algorithmic
+ * floating-point operations of those launches (2 per multiply-add of the
+ * method; recomputation and padding excluded). */
+fbsde_status fbsde_profile_enable(fbsde_ctx* ctx, int on);
+fbsde_status fbsde_profile_read(fbsde_ctx* ctx, int cls, double* ms_total, uint64_t* launches,
+                                double* flops);
+
+/* Kernels launched by this context since it was created. */
+uint64_t fbsde_launch_count(const fbsde_ctx* ctx);
+
+const char* fbsde_status_string(fbsde_status s);
+const char* fbsde_last_error(const fbsde_ctx* ctx);
+
+#ifdef __cplusplus
+}
+#endif
+#endif /* FBSDE_H */

@@ -1,0 +1,191 @@
+"""Torch-facing wrapper of libfbsde: tensor ownership and the current stream.
+
+PyTorch only allocates the caller-owned buffers (Theta, gradient, Adam
+moments, output scalars) and supplies the CUDA stream; every step of the
+method runs in the library's kernels.
+"""
+from __future__ import annotations
+
+from dataclasses import dataclass, field
+from typing import Optional, Sequence
+
+import numpy as np
+import torch
+
+from . import _lib as L
+
+_KIND = {"bsb": L.FBSDE_BSB, "hjb": L.FBSDE_HJB}
+_ARCH = {"fc": L.FBSDE_FC, "resnet": L.FBSDE_RESNET, "nais": L.FBSDE_NAIS}
+_ACT = {"sin": L.FBSDE_SIN, "tanh": L.FBSDE_TANH}
+_PREC = {"fp32": L.FBSDE_FP32, "bf16": L.FBSDE_BF16}
+
+
+@dataclass
+class ProblemSpec:
+    """FBSDE of Section 4 (mu = 0).  kind 'bsb' or 'hjb'."""
+    kind: str
+    D: int
+    N: int
+    M: int
+    x0: Sequence[float]
+    T: float = 1.0
+    r: float = 0.05
+    sigma: float = 0.4
+    terminal_grad_term: bool = False
+
+    def to_c(self):
+        x0 = np.ascontiguousarray(np.asarray(self.x0, dtype=np.float64))
+        if x0.shape != (self.D,):
+            raise ValueError(f"x0 must have {self.D} entries")
+        st = L.fbsde_problem(kind=_KIND[self.kind], D=self.D, N=self.N, M=self.M, T=self.T,
+                             r=self.r, sigma=self.sigma,
+                             x0_host=x0.ctypes.data_as(L.POINTER(L.c_double)),
+                             terminal_grad_term=int(bool(self.terminal_grad_term)))
+        return st, x0  # keep x0 alive while the struct is in use
+
+
+@dataclass
+class ArchSpec:
+    """Network of Section 3.1: kind 'fc' | 'resnet' | 'nais'; act 'sin' | 'tanh';
+    prec 'fp32' (CUDA-core form) | 'bf16' (tcgen05 tensor-core form)."""
+    kind: str
+    width: int
+    depth: int
+    act: str
+    prec: str = "fp32"
+    h: float = 1.0
+    eps: float = 0.01
+    proj_delta: float = 0.0
+
+    def to_c(self):
+        return L.fbsde_arch(kind=_ARCH[self.kind], width=self.width, depth=self.depth,
+                            act=_ACT[self.act], h=self.h, eps=self.eps,
+                            proj_delta=self.proj_delta, prec=_PREC[self.prec])
+
+
+def param_count(problem: ProblemSpec, arch: ArchSpec) -> int:
+    p, _keep = problem.to_c()
+    return L.fbsde_param_count(p, arch.to_c())
+
+
+class Solver:
+    """One libfbsde context on the current CUDA device and stream."""
+
+    def __init__(self, problem: ProblemSpec, arch: ArchSpec, seed: int = 0,
+                 stream: Optional[torch.cuda.Stream] = None, N_max: int = 0):
+        if not torch.cuda.is_available():
+            raise RuntimeError("libfbsde needs a CUDA device")
+        self.problem, self.arch, self.seed = problem, arch, seed
+        self.stream = stream or torch.cuda.current_stream()
+        p, self._x0 = problem.to_c()
+        self.ctx = L.fbsde_create(p, arch.to_c(), seed, self.stream.cuda_stream, N_max)
+        self.n_params = L.fbsde_num_params(self.ctx)
+        dev = torch.device("cuda", torch.cuda.current_device())
+        self.device = dev
+        self._loss = torch.zeros(1, device=dev)
+        self._y0 = torch.zeros(1, device=dev)
+
+    def close(self):
+        if getattr(self, "ctx", None) is not None:
+            L.fbsde_destroy(self.ctx)
+            self.ctx = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+    def _check_theta(self, t: torch.Tensor):
+        if t.dtype != torch.float32 or not t.is_cuda or not t.is_contiguous() or t.numel() != self.n_params:
+            raise ValueError(f"expected a contiguous CUDA float32 tensor of {self.n_params} entries")
+
+    def init_params(self) -> torch.Tensor:
+        theta = torch.empty(self.n_params, device=self.device)
+        L.fbsde_init_params(self.ctx, theta.data_ptr())
+        return theta
+
+    def rollout_loss(self, theta: torch.Tensor, iteration: int):
+        self._check_theta(theta)
+        loss = torch.empty(1, device=self.device)
+        y0 = torch.empty(1, device=self.device)
+        L.fbsde_rollout_loss(self.ctx, theta.data_ptr(), iteration, loss.data_ptr(), y0.data_ptr())
+        return loss, y0
+
+    def rollout_grad(self, theta: torch.Tensor, iteration: int, grad: Optional[torch.Tensor] = None):
+        self._check_theta(theta)
+        loss = torch.empty(1, device=self.device)
+        y0 = torch.empty(1, device=self.device)
+        if grad is None:
+            grad = torch.empty(self.n_params, device=self.device)
+        L.fbsde_rollout_grad(self.ctx, theta.data_ptr(), iteration, loss.data_ptr(), y0.data_ptr(),
+                             grad.data_ptr())
+        return loss, y0, grad
+
+    def train_step(self, theta, m, v, step: int, lr: float = 1e-3, loss=None, y0=None):
+        for t in (theta, m, v):
+            self._check_theta(t)
+        loss = self._loss if loss is None else loss
+        y0 = self._y0 if y0 is None else y0
+        L.fbsde_train_step(self.ctx, theta.data_ptr(), m.data_ptr(), v.data_ptr(), step, lr,
+                           loss.data_ptr(), y0.data_ptr())
+        return loss, y0
+
+    def rollout_detail(self, theta: torch.Tensor, iteration: int):
+        self._check_theta(theta)
+        P = self.problem.M * (self.problem_N + 1)
+        Y = torch.empty(P, device=self.device)
+        Z = torch.empty(P * self.problem.D, device=self.device)
+        pl = torch.empty(self.problem.M, device=self.device)
+        L.fbsde_rollout_detail(self.ctx, theta.data_ptr(), iteration, Y.data_ptr(), Z.data_ptr(),
+                               pl.data_ptr())
+        N1 = self.problem_N + 1
+        return Y.view(N1, self.problem.M), Z.view(N1, self.problem.M, self.problem.D), pl
+
+    def sample_paths(self, iteration: int):
+        M, D, N = self.problem.M, self.problem.D, self.problem_N
+        dW = torch.empty(N, M, D, device=self.device)
+        X = torch.empty(N + 1, M, D, device=self.device)
+        L.fbsde_sample_paths(self.ctx, iteration, dW.data_ptr(), X.data_ptr())
+        return dW, X
+
+    @property
+    def problem_N(self) -> int:
+        return getattr(self, "_level", self.problem.N)
+
+    def set_level(self, N: int):
+        L.fbsde_set_level(self.ctx, N)
+        self._level = N
+
+    def set_x0(self, x0):
+        L.fbsde_set_x0(self.ctx, list(x0))
+
+    def check_finite(self):
+        L.fbsde_check_finite(self.ctx)
+
+
+def philox4x32_10(ctr: torch.Tensor, key0: int, key1: int) -> torch.Tensor:
+    """Raw Philox4x32-10 blocks on the GPU: ctr int32 [n, 4] (bit patterns) -> [n, 4]."""
+    assert ctr.is_cuda and ctr.dtype == torch.int32 and ctr.is_contiguous() and ctr.shape[-1] == 4
+    out = torch.empty_like(ctr)
+    L.fbsde_philox4x32_10(ctr.data_ptr(), key0 & 0xFFFFFFFF, key1 & 0xFFFFFFFF, ctr.shape[0],
+                          out.data_ptr(), torch.cuda.current_stream().cuda_stream)
+    return out
+
+
+class RolloutLoss(torch.autograd.Function):
+    """loss(Theta) of Eq. (loss) as an autograd node: forward runs the rollout
+    and the hand-written adjoint in one library call; backward scales the
+    stored gradient by the incoming scalar."""
+
+    @staticmethod
+    def forward(ctx, theta: torch.Tensor, solver: Solver, iteration: int):
+        loss, y0, grad = solver.rollout_grad(theta.detach().contiguous(), iteration)
+        ctx.save_for_backward(grad)
+        ctx.mark_non_differentiable(y0)
+        return loss[0], y0[0]
+
+    @staticmethod
+    def backward(ctx, gloss, gy0):
+        grad, = ctx.saved_tensors
+        return gloss * grad, None, None

@@ -1,0 +1,57 @@
+"""Named workloads: problem + architecture specifications with their seeds.
+
+Every input of the method is synthetic by construction: the Brownian paths are
+the method's own draws (Philox, keyed by the seed) and Theta_0 is a seeded
+Xavier initialisation.  The shapes follow Section 4 (Black--Scholes--Barenblatt
+with d = 100, r = 0.05, sigma = 0.4; HJB with d = 100, T = 1, x0 = 0) at the
+sizes used for measurement.  This module holds specifications only.
+"""
+from __future__ import annotations
+
+from dataclasses import dataclass, replace
+
+from .solver import ArchSpec, ProblemSpec
+
+
+def bsb_x0(D: int):
+    """x0 = (1, 0.5, 1, 0.5, ...); with D = 100 the closed form gives
+    u(0, x0) = 62.5 exp(0.21) ~ 77.1, the value the paper's figure marks."""
+    return [1.0 if i % 2 == 0 else 0.5 for i in range(D)]
+
+
+@dataclass(frozen=True)
+class Workload:
+    name: str
+    problem: ProblemSpec
+    arch: ArchSpec
+    seed: int = 0
+    adam_steps: int = 0
+    lr: float = 1e-3
+
+    def with_prec(self, prec: str) -> "Workload":
+        return replace(self, arch=replace(self.arch, prec=prec))
+
+
+WORKLOADS = {
+    # 10-D BSB, N = 8 steps, M = 64 paths, FC 4 x 64 sin: the small case
+    "bsb_d10_n8_m64_fc4x64_sin": Workload(
+        "bsb_d10_n8_m64_fc4x64_sin",
+        ProblemSpec(kind="bsb", D=10, N=8, M=64, x0=bsb_x0(10)),
+        ArchSpec(kind="fc", width=64, depth=4, act="sin"), seed=0, adam_steps=200),
+    # 100-D BSB, N = 64, M = 4096, ResNet 5 blocks x 256 tanh: the measured workload
+    "bsb_d100_n64_m4096_resnet5x256_tanh": Workload(
+        "bsb_d100_n64_m4096_resnet5x256_tanh",
+        ProblemSpec(kind="bsb", D=100, N=64, M=4096, x0=bsb_x0(100)),
+        ArchSpec(kind="resnet", width=256, depth=5, act="tanh"), seed=0, adam_steps=5000),
+    # 100-D HJB, N = 64, M = 8192, x0 = 0, NAIS 6 blocks x 256 tanh
+    "hjb_d100_n64_m8192_nais6x256_tanh": Workload(
+        "hjb_d100_n64_m8192_nais6x256_tanh",
+        ProblemSpec(kind="hjb", D=100, N=64, M=8192, x0=[0.0] * 100),
+        ArchSpec(kind="nais", width=256, depth=6, act="tanh"), seed=0, adam_steps=5000),
+}
+
+# Closed-form anchors (Section 4): BSB u(0, x0) and HJB u(0, 0) (Cole-Hopf,
+# chi-square quadrature), used for the accuracy of a trained Y_0.
+BSB_Y0_D100 = 77.10487946
+BSB_Y0_D10 = 7.710487946
+HJB_U00_D100 = 4.590162

@@ -1,0 +1,223 @@
+"""Parity of the CUDA path with the FP64 oracle, through the C ABI.
+
+Tolerances: the FP32 form must match within 1e-5 (relative, scale-aware:
+max|gpu - oracle| / max|oracle| per quantity); the BF16 form within 2e-2.
+Philox words are compared bit for bit."""
+import numpy as np
+import pytest
+
+torch = pytest.importorskip("torch")
+
+from oracle import fbsde as F
+from oracle import philox
+from tests.helpers import oracle_specs, rel, rel_max
+
+pytestmark = pytest.mark.gpu
+
+TOL = {"fp32": 1e-5, "bf16": 2e-2}
+
+
+@pytest.fixture(scope="module")
+def P():
+    import paper_1910_11623_gb300 as P
+    if not torch.cuda.is_available():
+        pytest.skip("no CUDA device")
+    return P
+
+
+def _solver(P, problem, arch, seed=0, N_max=0):
+    return P.Solver(problem, arch, seed=seed, N_max=N_max)
+
+
+def _theta_pair(P, s, problem, arch, seed, perturb=0.0):
+    """Theta as the oracle sees it (FP64) and as the GPU sees it (the same
+    values rounded to FP32)."""
+    op, oa = oracle_specs(problem, arch)
+    th = F.init_params(op, oa, seed)
+    if perturb:
+        th = th + perturb * np.random.default_rng(seed + 1).standard_normal(th.size)
+        if arch.kind == "nais":
+            th = F.nais_project(th, op, oa)
+    th32 = th.astype(np.float32)
+    return th32.astype(np.float64), torch.tensor(th32, device="cuda")
+
+
+# ------------------------------------------------------------------ noise
+
+def test_philox_words_bit_exact(P, golden_dir):
+    rng = np.random.default_rng(0)
+    ctr = rng.integers(0, 2**32, size=(4096, 4), dtype=np.uint64)
+    ctr[:3] = [[0, 0, 0, 0], [0xFFFFFFFF] * 4, [0x243F6A88, 0x85A308D3, 0x13198A2E, 0x03707344]]
+    for key in [(0, 0), (0xFFFFFFFF, 0xFFFFFFFF), (0xA4093822, 0x299F31D0), (12345, 678)]:
+        want = philox.philox4x32_10(ctr, np.array(key, dtype=np.uint64))
+        got = P.philox4x32_10(torch.tensor(ctr.astype(np.uint32).view(np.int32), device="cuda"), *key)
+        got = got.cpu().numpy().view(np.uint32)
+        assert np.array_equal(got, want), key
+
+
+@pytest.mark.parametrize("kind,D,N,M", [("bsb", 10, 8, 64), ("hjb", 13, 5, 37), ("bsb", 1, 1, 1)])
+def test_increments_and_paths(P, kind, D, N, M):
+    x0 = [1.0 if i % 2 == 0 else 0.5 for i in range(D)] if kind == "bsb" else [0.0] * D
+    prob = P.ProblemSpec(kind=kind, D=D, N=N, M=M, x0=x0)
+    arch = P.ArchSpec(kind="fc", width=16, depth=1, act="tanh")
+    s = _solver(P, prob, arch, seed=0xABCDEF0123)
+    dW, X = s.sample_paths(7)
+    op, _ = oracle_specs(prob, arch)
+    dWo, Xo = F.sample_paths(op, 0xABCDEF0123, 7)
+    assert rel_max(dW.cpu().numpy(), dWo) < 2e-6
+    assert rel_max(X.cpu().numpy(), Xo) < 1e-5
+    s.close()
+
+
+def test_init_matches_oracle(P):
+    for kind in ["fc", "resnet", "nais"]:
+        prob = P.ProblemSpec(kind="bsb", D=10, N=4, M=8, x0=[1.0] * 10)
+        arch = P.ArchSpec(kind=kind, width=32, depth=3, act="tanh")
+        s = _solver(P, prob, arch, seed=5)
+        th = s.init_params().cpu().numpy()
+        op, oa = oracle_specs(prob, arch)
+        assert rel_max(th, F.init_params(op, oa, 5)) < 2e-6
+        s.close()
+
+
+# ------------------------------------------------------------------ loss, Y, Z, gradient
+
+def _check_eval(P, prob, arch, seed=3, it=11, perturb=0.1, tol=None):
+    tol = tol or TOL[arch.prec]
+    s = _solver(P, prob, arch, seed=seed)
+    th64, th = _theta_pair(P, s, prob, arch, seed, perturb)
+    op, oa = oracle_specs(prob, arch)
+    ro, g = F.rollout_grad(op, oa, th64, seed, it)
+    loss, y0, grad = s.rollout_grad(th, it)
+    Y, Z, pl = s.rollout_detail(th, it)
+    torch.cuda.synchronize()
+    errs = {
+        "loss": rel(loss.item(), ro.loss),
+        "y0": rel(y0.item(), ro.y0),
+        "Y": rel_max(Y.cpu().numpy(), ro.Y),
+        "Z": rel_max(Z.cpu().numpy(), ro.Z),
+        "path_loss": rel_max(pl.cpu().numpy(), ro.path_loss),
+        "grad": rel_max(grad.cpu().numpy(), g),
+    }
+    s.close()
+    bad = {k: v for k, v in errs.items() if not v <= tol}
+    assert not bad, f"{errs}"
+    return errs
+
+
+def test_small_workload_fp32(P):
+    w = P.workloads.WORKLOADS["bsb_d10_n8_m64_fc4x64_sin"]
+    _check_eval(P, w.problem, w.arch, seed=w.seed, perturb=0.0)
+
+
+@pytest.mark.parametrize("kind", ["fc", "resnet", "nais"])
+@pytest.mark.parametrize("pk", ["bsb", "hjb"])
+@pytest.mark.parametrize("act", ["sin", "tanh"])
+def test_arch_problem_grid_fp32(P, kind, pk, act):
+    D = 6
+    x0 = [1.0, 0.5] * 3 if pk == "bsb" else [0.0] * D
+    prob = P.ProblemSpec(kind=pk, D=D, N=5, M=24, x0=x0, terminal_grad_term=(kind == "resnet"))
+    arch = P.ArchSpec(kind=kind, width=32, depth=3, act=act, h=0.5 if kind == "nais" else 1.0)
+    _check_eval(P, prob, arch)
+
+
+def test_ragged_tiles_fp32(P):
+    # P = 37 * 8 = 296 points (two full 128-row tiles and a tail), width 48
+    # (a partial 128-column tile), D = 13 (not a multiple of 4).
+    prob = P.ProblemSpec(kind="bsb", D=13, N=7, M=37, x0=[0.7] * 13)
+    arch = P.ArchSpec(kind="resnet", width=48, depth=2, act="tanh")
+    _check_eval(P, prob, arch)
+
+
+@pytest.mark.parametrize("case", ["D1_N1_M1", "depth0", "M1"])
+def test_edge_cases_fp32(P, case):
+    if case == "D1_N1_M1":
+        prob = P.ProblemSpec(kind="hjb", D=1, N=1, M=1, x0=[0.3])
+        arch = P.ArchSpec(kind="fc", width=16, depth=1, act="sin")
+    elif case == "depth0":
+        prob = P.ProblemSpec(kind="bsb", D=5, N=3, M=9, x0=[1.0] * 5, terminal_grad_term=True)
+        arch = P.ArchSpec(kind="resnet", width=16, depth=0, act="tanh")
+    else:
+        prob = P.ProblemSpec(kind="bsb", D=8, N=16, M=1, x0=[1.0, 0.5] * 4)
+        arch = P.ArchSpec(kind="nais", width=16, depth=2, act="tanh")
+    _check_eval(P, prob, arch)
+
+
+def test_train_steps_fp32(P):
+    # three Adam steps from the same Theta: trajectories agree to FP32 accuracy
+    w = P.workloads.WORKLOADS["bsb_d10_n8_m64_fc4x64_sin"]
+    s = _solver(P, w.problem, w.arch, seed=0)
+    th64, th = _theta_pair(P, s, w.problem, w.arch, 0)
+    m = torch.zeros_like(th); v = torch.zeros_like(th)
+    op, oa = oracle_specs(w.problem, w.arch)
+    mo, vo = np.zeros_like(th64), np.zeros_like(th64)
+    for step in range(1, 4):
+        loss, y0 = s.train_step(th, m, v, step, 1e-3)
+        lo, y0o, th64, mo, vo = F.train_step(op, oa, th64, mo, vo, 0, step, 1e-3)
+        assert rel(loss.item(), lo) < 1e-5 and rel(y0.item(), y0o) < 1e-5
+    assert rel_max(th.cpu().numpy(), th64) < 1e-5
+    s.close()
+
+
+def test_nais_train_step_projects(P):
+    prob = P.ProblemSpec(kind="hjb", D=6, N=4, M=16, x0=[0.0] * 6)
+    arch = P.ArchSpec(kind="nais", width=32, depth=2, act="tanh", h=1.0)
+    s = _solver(P, prob, arch, seed=1)
+    th = s.init_params()
+    m = torch.zeros_like(th); v = torch.zeros_like(th)
+    for step in range(1, 4):
+        s.train_step(th, m, v, step, 0.05)
+    op, oa = oracle_specs(prob, arch)
+    parts = F.unpack(th.cpu().numpy().astype(np.float64), op, oa)
+    for l in (1, 2):
+        R = parts[f"R_{l}"]
+        assert np.linalg.norm(R.T @ R, "fro") <= oa.delta * (1 + 1e-5)
+    s.close()
+
+
+def test_level_switch_and_x0(P):
+    prob = P.ProblemSpec(kind="bsb", D=4, N=8, M=16, x0=[1.0] * 4)
+    arch = P.ArchSpec(kind="fc", width=16, depth=2, act="tanh")
+    s = _solver(P, prob, arch, seed=2, N_max=16)
+    th64, th = _theta_pair(P, s, prob, arch, 2, 0.1)
+    for N in [2, 16, 8]:
+        s.set_level(N)
+        loss, y0 = s.rollout_loss(th, 3)
+        op, oa = oracle_specs(P.ProblemSpec(kind="bsb", D=4, N=N, M=16, x0=[1.0] * 4), arch)
+        assert rel(loss.item(), F.rollout_loss(op, oa, th64, 2, 3).loss) < 1e-5
+    s.set_x0([0.9, 1.1, 1.0, 0.8])
+    loss, y0 = s.rollout_loss(th, 3)
+    op, oa = oracle_specs(P.ProblemSpec(kind="bsb", D=4, N=8, M=16, x0=[0.9, 1.1, 1.0, 0.8]), arch)
+    assert rel(loss.item(), F.rollout_loss(op, oa, th64, 2, 3).loss) < 1e-5
+    with pytest.raises(Exception):
+        s.set_level(17)
+    s.close()
+
+
+def test_autograd_function(P):
+    prob = P.ProblemSpec(kind="bsb", D=4, N=4, M=8, x0=[1.0] * 4)
+    arch = P.ArchSpec(kind="resnet", width=16, depth=2, act="tanh")
+    s = _solver(P, prob, arch, seed=4)
+    th = s.init_params().requires_grad_(True)
+    loss, y0 = P.RolloutLoss.apply(th, s, 5)
+    (3.0 * loss).backward()
+    _, _, g = s.rollout_grad(th.detach(), 5)
+    assert torch.allclose(th.grad, 3.0 * g)
+    s.close()
+
+
+def test_nonfinite_is_reported(P):
+    prob = P.ProblemSpec(kind="bsb", D=4, N=4, M=8, x0=[1.0] * 4)
+    arch = P.ArchSpec(kind="fc", width=16, depth=1, act="tanh")
+    s = _solver(P, prob, arch)
+    th = s.init_params()
+    s.rollout_grad(th, 1)
+    s.check_finite()
+    th[0] = float("nan")
+    s.rollout_grad(th, 1)
+    from paper_1910_11623_gb300 import _lib as L
+    with pytest.raises(L.FBSDEError) as ei:
+        s.check_finite()
+    assert ei.value.status == L.FBSDE_ERR_NONFINITE
+    s.check_finite()  # the flag is cleared once reported
+    s.close()
