@@ -178,6 +178,19 @@ fbsde_status fbsde_sample_paths(fbsde_ctx* ctx, uint64_t iter, float* dW_dev, fl
 fbsde_status fbsde_philox4x32_10(const uint32_t* ctr_dev, uint32_t key0, uint32_t key1,
                                  size_t count, uint32_t* out_dev, void* cuda_stream);
 
+/* The tensor-core contraction every network layer of the BF16 form is built
+ * on (Section 2.2: the same network is evaluated at all M (N+1) points, so each
+ * layer is one product over points): C[m][n] = sum_k A(m,k) B(n,k) with BF16
+ * operands (raw 16-bit patterns) and FP32 accumulation, on tcgen05.
+ *   trans = 0: A [rows x K] row-major (lda), B [N x K] row-major (ldb);
+ *   trans = 1: A [K x rows] row-major (lda), B [K x N] row-major (ldb), i.e.
+ *              the contraction runs over the leading index (weight gradients).
+ * C [rows x N] row-major (ldc), FP32, overwritten.  Requires rows, K >= 1,
+ * N a multiple of 16 in [16, 256], lda and ldb multiples of 8, A and B
+ * 16-byte aligned.  Runs on `cuda_stream` and waits for completion. */
+fbsde_status fbsde_gemm_bf16(const void* A_dev, const void* B_dev, float* C_dev, int rows, int N, int K,
+                             int lda, int ldb, int ldc, int trans, void* cuda_stream);
+
 /* Multilevel discretisation (Section 3.2): switch the context to N_level
  * Euler steps (Delta t = T / N_level), 1 <= N_level <= N_max.  Theta and the
  * Adam moments are untouched, so training continues on the finer grid. */

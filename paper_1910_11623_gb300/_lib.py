@@ -47,6 +47,8 @@ SIGNATURES = {
     "fbsde_rollout_detail": (c_int, [c_void_p, c_void_p, c_uint64, c_void_p, c_void_p, c_void_p]),
     "fbsde_sample_paths": (c_int, [c_void_p, c_uint64, c_void_p, c_void_p]),
     "fbsde_philox4x32_10": (c_int, [c_void_p, c_uint32, c_uint32, c_size_t, c_void_p, c_void_p]),
+    "fbsde_gemm_bf16": (c_int, [c_void_p, c_void_p, c_void_p, c_int, c_int, c_int, c_int, c_int, c_int,
+                                c_int, c_void_p]),
     "fbsde_set_level": (c_int, [c_void_p, c_int]),
     "fbsde_set_x0": (c_int, [c_void_p, POINTER(c_double)]),
     "fbsde_check_finite": (c_int, [c_void_p]),
@@ -159,6 +161,12 @@ def fbsde_sample_paths(ctx, it: int, dW_ptr: int, X_ptr: int):
 def fbsde_philox4x32_10(ctr_ptr: int, key0: int, key1: int, count: int, out_ptr: int, stream: int):
     check(load().fbsde_philox4x32_10(c_void_p(ctr_ptr), key0, key1, count, c_void_p(out_ptr),
                                      c_void_p(stream or None)), "fbsde_philox4x32_10")
+
+
+def fbsde_gemm_bf16(A_ptr: int, B_ptr: int, C_ptr: int, rows: int, N: int, K: int, lda: int, ldb: int,
+                    ldc: int, trans: int, stream: int):
+    check(load().fbsde_gemm_bf16(c_void_p(A_ptr), c_void_p(B_ptr), c_void_p(C_ptr), rows, N, K, lda, ldb, ldc,
+                                 trans, c_void_p(stream or None)), "fbsde_gemm_bf16")
 
 
 def fbsde_set_level(ctx, N: int):

@@ -22,12 +22,6 @@
 
 namespace fbsde {
 
-static inline float layer_skip(const fbsde_ctx* c, int l) {
-    return (l == 0 || c->akind == FBSDE_FC) ? 0.f : 1.f;
-}
-static inline float layer_scale(const fbsde_ctx* c, int l) {
-    return (l > 0 && c->akind == FBSDE_NAIS) ? (float)c->h : 1.f;
-}
 // Matrix acting on h in layer l >= 1: W_l, or the NAIS A_l formed per call.
 static inline const float* layer_matrix(const fbsde_ctx* c, const float* theta, int l) {
     return c->akind == FBSDE_NAIS ? c->Amat[l] : theta + c->pl.W[l];
@@ -279,6 +273,33 @@ static fbsde_status tn_reduce(fbsde_ctx* c, GemmArgs g, int c0, int nc, float* o
     GEMM_LAUNCH(c, PROF_WGRAD, true, true, g, splits, (EpiPartial{c->part, g.Mrows, g.Ncols}));
     k_reduce_part<<<nblk((size_t)g.Mrows * nc, 256), 256, 0, c->stream>>>(
         c->part, splits, g.Mrows, g.Ncols, c0, nc, out, ld, off);
+    FBSDE_CK_LAUNCH(c);
+    return FBSDE_OK;
+}
+
+// ---------------------------------------------------------------- shared with the BF16 form
+
+fbsde_status launch_rowdot(fbsde_ctx* c, const float* h, const float* theta, float* y) {
+    const size_t P = c->P();
+    k_rowdot<<<nblk(P * 32, 256), 256, 0, c->stream>>>(P, c->w, h, theta + c->pl.wo, theta + c->pl.bo, y);
+    FBSDE_CK_LAUNCH(c);
+    return FBSDE_OK;
+}
+
+// d loss / d R_l = -R_l (dA_l + dA_l^T) from the gradient dA_l in c->gA[l].
+fbsde_status nais_chain_R(fbsde_ctx* c, const float* theta, float* grad, int l) {
+    const int w = c->w;
+    k_sym<<<nblk((size_t)w * w, 256), 256, 0, c->stream>>>(w, c->gA[l], c->sym);
+    FBSDE_CK_LAUNCH(c);
+    GemmArgs gr{};
+    gr.npairs = 1; gr.Mrows = w; gr.Ncols = w; gr.kchunk = 1 << 30;
+    gr.pair[0] = {theta + c->pl.W[l], c->sym, w, w, w};
+    GEMM_LAUNCH(c, PROF_WGRAD, false, true, gr, 1, (EpiNeg{grad + c->pl.W[l], w}));
+    return FBSDE_OK;
+}
+
+fbsde_status launch_check_finite(fbsde_ctx* c, const float* x, size_t n) {
+    k_check_finite<<<nblk(n, 256), 256, 0, c->stream>>>(n, x, c->nonfinite);
     FBSDE_CK_LAUNCH(c);
     return FBSDE_OK;
 }

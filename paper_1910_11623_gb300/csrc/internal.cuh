@@ -160,6 +160,20 @@ fbsde_status bf16_prepare_weights(fbsde_ctx* ctx, const float* theta);
 fbsde_status bf16_forward(fbsde_ctx* ctx, const float* theta);
 fbsde_status bf16_backward(fbsde_ctx* ctx, const float* theta, float* grad);
 
+// Helpers of the FP32 form reused by the BF16 form.
+fbsde_status launch_rowdot(fbsde_ctx* c, const float* h, const float* theta, float* y);
+fbsde_status nais_chain_R(fbsde_ctx* c, const float* theta, float* grad, int l);
+fbsde_status launch_check_finite(fbsde_ctx* c, const float* x, size_t n);
+
+// Skip s and scale c of layer l in h_l = s h_{l-1} + c act(a_l): (0, 1) for
+// the lift and FC layers, (1, 1) for ResNet blocks, (1, h) for NAIS blocks.
+inline float layer_skip(const fbsde_ctx* c, int l) {
+    return (l == 0 || c->akind == FBSDE_FC) ? 0.f : 1.f;
+}
+inline float layer_scale(const fbsde_ctx* c, int l) {
+    return (l > 0 && c->akind == FBSDE_NAIS) ? (float)c->h : 1.f;
+}
+
 // Adam (adam.cu).
 fbsde_status launch_adam(fbsde_ctx* ctx, float* theta, const float* grad, float* m, float* v,
                          uint64_t step, float lr);

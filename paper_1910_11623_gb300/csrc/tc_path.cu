@@ -1,20 +1,646 @@
-// BF16 tensor-core form of the network sweeps (tcgen05, sm_103a).
+// BF16 form of the network sweeps: every contraction runs on the tcgen05
+// tensor cores (BF16 operands, FP32 accumulation) with the per-layer
+// elementwise work fused into the GEMM epilogue.  The sweeps are the ones of
+// the FP32 form (forward, Z-reverse, tangent, adjoint, weight gradients; see
+// fp32_path.cu); GEMM operands are stored in BF16, every residual stream,
+// pre-activation and reduction stays in FP32.
+#include <cuda.h>
+#include <cudaTypedefs.h>
+#include <cuda_bf16.h>
 #include <cuda_runtime.h>
 
+#include <cstring>
+#include <string>
+
 #include "internal.cuh"
+#include "tc_gemm.cuh"
 
 namespace fbsde {
 
+typedef __nv_bfloat16 bf16;
+
+static inline size_t rup(size_t x, size_t m) { return (x + m - 1) / m * m; }
+static inline unsigned nblk(size_t n, int bs) { return (unsigned)((n + bs - 1) / bs); }
+
+// ------------------------------------------------------------------ tensor maps
+
+static PFN_cuTensorMapEncodeTiled_v12000 encode_fn() {
+    static PFN_cuTensorMapEncodeTiled_v12000 fn = nullptr;
+    if (!fn) {
+        void* p = nullptr;
+        cudaDriverEntryPointQueryResult q;
+        if (cudaGetDriverEntryPointByVersion("cuTensorMapEncodeTiled", &p, 12000, cudaEnableDefault, &q) ==
+                cudaSuccess &&
+            q == cudaDriverEntryPointSuccess)
+            fn = (PFN_cuTensorMapEncodeTiled_v12000)p;
+    }
+    return fn;
+}
+
+// Row-major BF16 matrix [outer x inner] with row stride ld (elements), box
+// {64, box_outer}, 128-byte swizzle, zero fill outside the matrix.
+static bool map2d(CUtensorMap* m, const void* base, uint64_t inner, uint64_t outer, uint64_t ld,
+                  uint32_t box_outer) {
+    auto fn = encode_fn();
+    if (!fn) return false;
+    cuuint64_t dims[2] = {inner, outer};
+    cuuint64_t strides[1] = {ld * sizeof(bf16)};
+    cuuint32_t box[2] = {64, box_outer};
+    cuuint32_t es[2] = {1, 1};
+    return fn(m, CU_TENSOR_MAP_DATA_TYPE_BFLOAT16, 2, const_cast<void*>(base), dims, strides, box, es,
+              CU_TENSOR_MAP_INTERLEAVE_NONE, CU_TENSOR_MAP_SWIZZLE_128B, CU_TENSOR_MAP_L2_PROMOTION_L2_256B,
+              CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE) == CUDA_SUCCESS;
+}
+
+// ------------------------------------------------------------------ workspace
+
 struct Bf16Work {
-    int unused;
+    int Dp, Dn, wp;  // D padded to 64 (operand rows), D padded to 16 (MMA N), w padded to 64
+    void* mem = nullptr;
+    bf16 *Xb, *Vb;
+    bf16 *Hb[kMaxDepth + 1], *Eb[kMaxDepth + 1], *HDb[kMaxDepth + 1], *ABb[kMaxDepth + 1];
+    float *Af[kMaxDepth + 1], *Hf[kMaxDepth + 1], *Gf[kMaxDepth + 1], *HDf[kMaxDepth + 1];
+    float *Sf[kMaxDepth + 1], *HBf[kMaxDepth + 1];
+    bf16 *Winx, *WinxT, *W[kMaxDepth + 1], *WT[kMaxDepth + 1], *Bx[kMaxDepth + 1], *BxT[kMaxDepth + 1];
+    float* colpart;
+    int* err;
+    // NT operand maps (box rows 128)
+    CUtensorMap mXb, mVb, mHb[kMaxDepth + 1], mEb[kMaxDepth + 1], mHDb[kMaxDepth + 1], mABb[kMaxDepth + 1];
+    // weight maps (box rows = N of the contraction)
+    CUtensorMap mWinx, mWinxT, mW[kMaxDepth + 1], mWT[kMaxDepth + 1], mBx[kMaxDepth + 1], mBxT[kMaxDepth + 1];
+    // MN-major maps for the weight gradients (box {64, 64})
+    CUtensorMap tX, tV, tH[kMaxDepth + 1], tE[kMaxDepth + 1], tHD[kMaxDepth + 1], tAB[kMaxDepth + 1];
 };
 
-fbsde_status bf16_create(fbsde_ctx* ctx) {
-    return set_err(ctx, FBSDE_ERR_UNSUPPORTED, "BF16 form not built yet");
+constexpr int kColSplits = 128;
+
+fbsde_status bf16_create(fbsde_ctx* c) {
+    Bf16Work* b = new (std::nothrow) Bf16Work();
+    if (!b) return set_err(c, FBSDE_ERR_OOM, "host allocation failed");
+    c->bf = b;
+    const int w = c->w, L = c->L, D = c->D;
+    b->Dp = (int)rup(D, 64);
+    b->Dn = (int)rup(D, 16);
+    b->wp = (int)rup(w, 64);
+    const size_t Pm = c->Pmax();
+    size_t bytes = 0;
+    auto add = [&](size_t n) { bytes += rup(n, 256); };
+    add(2 * Pm * b->Dp * sizeof(bf16));
+    for (int l = 0; l <= L; ++l) {
+        for (int k = 0; k < 4; ++k) add(Pm * b->wp * sizeof(bf16));
+        for (int k = 0; k < 6; ++k) add(Pm * w * sizeof(float));
+    }
+    add((size_t)w * b->Dp * 2); add((size_t)b->Dn * b->wp * 2);
+    for (int l = 1; l <= L; ++l) {
+        add((size_t)w * b->wp * 2); add((size_t)w * b->wp * 2);
+        add((size_t)w * b->Dp * 2); add((size_t)b->Dn * b->wp * 2);
+    }
+    add((size_t)kColSplits * (rup(w, 16) + 16) * sizeof(float));
+    add(256);
+    cudaError_t e = cudaMalloc(&b->mem, bytes);
+    if (e != cudaSuccess) {
+        cudaGetLastError();
+        return set_err(c, e == cudaErrorMemoryAllocation ? FBSDE_ERR_OOM : FBSDE_ERR_CUDA,
+                       std::string("cudaMalloc BF16 workspace (") + std::to_string(bytes >> 20) + " MiB): " +
+                           cudaGetErrorString(e));
+    }
+    FBSDE_CK(c, cudaMemset(b->mem, 0, bytes));
+    char* cur = (char*)b->mem;
+    auto take = [&](size_t n) { char* p = cur; cur += rup(n, 256); return (void*)p; };
+    b->Xb = (bf16*)take(Pm * b->Dp * sizeof(bf16));
+    b->Vb = (bf16*)take(Pm * b->Dp * sizeof(bf16));
+    for (int l = 0; l <= L; ++l) {
+        b->Hb[l] = (bf16*)take(Pm * b->wp * 2); b->Eb[l] = (bf16*)take(Pm * b->wp * 2);
+        b->HDb[l] = (bf16*)take(Pm * b->wp * 2); b->ABb[l] = (bf16*)take(Pm * b->wp * 2);
+        b->Af[l] = (float*)take(Pm * w * 4); b->Hf[l] = (float*)take(Pm * w * 4);
+        b->Gf[l] = (float*)take(Pm * w * 4); b->HDf[l] = (float*)take(Pm * w * 4);
+        b->Sf[l] = (float*)take(Pm * w * 4); b->HBf[l] = (float*)take(Pm * w * 4);
+    }
+    b->Winx = (bf16*)take((size_t)w * b->Dp * 2);
+    b->WinxT = (bf16*)take((size_t)b->Dn * b->wp * 2);
+    for (int l = 1; l <= L; ++l) {
+        b->W[l] = (bf16*)take((size_t)w * b->wp * 2); b->WT[l] = (bf16*)take((size_t)w * b->wp * 2);
+        b->Bx[l] = (bf16*)take((size_t)w * b->Dp * 2); b->BxT[l] = (bf16*)take((size_t)b->Dn * b->wp * 2);
+    }
+    b->colpart = (float*)take((size_t)kColSplits * (rup(w, 16) + 16) * sizeof(float));
+    b->err = (int*)take(256);
+
+    bool ok = true;
+    const uint64_t P64 = Pm;
+    ok &= map2d(&b->mXb, b->Xb, b->Dp, P64, b->Dp, 128);
+    ok &= map2d(&b->mVb, b->Vb, b->Dp, P64, b->Dp, 128);
+    ok &= map2d(&b->tX, b->Xb, b->Dp, P64, b->Dp, 64);
+    ok &= map2d(&b->tV, b->Vb, b->Dp, P64, b->Dp, 64);
+    for (int l = 0; l <= L; ++l) {
+        ok &= map2d(&b->mHb[l], b->Hb[l], b->wp, P64, b->wp, 128);
+        ok &= map2d(&b->mEb[l], b->Eb[l], b->wp, P64, b->wp, 128);
+        ok &= map2d(&b->mHDb[l], b->HDb[l], b->wp, P64, b->wp, 128);
+        ok &= map2d(&b->mABb[l], b->ABb[l], b->wp, P64, b->wp, 128);
+        ok &= map2d(&b->tH[l], b->Hb[l], b->wp, P64, b->wp, 64);
+        ok &= map2d(&b->tE[l], b->Eb[l], b->wp, P64, b->wp, 64);
+        ok &= map2d(&b->tHD[l], b->HDb[l], b->wp, P64, b->wp, 64);
+        ok &= map2d(&b->tAB[l], b->ABb[l], b->wp, P64, b->wp, 64);
+    }
+    ok &= map2d(&b->mWinx, b->Winx, b->Dp, w, b->Dp, w);
+    ok &= map2d(&b->mWinxT, b->WinxT, b->wp, b->Dn, b->wp, b->Dn);
+    for (int l = 1; l <= L; ++l) {
+        ok &= map2d(&b->mW[l], b->W[l], b->wp, w, b->wp, w);
+        ok &= map2d(&b->mWT[l], b->WT[l], b->wp, w, b->wp, w);
+        ok &= map2d(&b->mBx[l], b->Bx[l], b->Dp, w, b->Dp, w);
+        ok &= map2d(&b->mBxT[l], b->BxT[l], b->wp, b->Dn, b->wp, b->Dn);
+    }
+    if (!ok) return set_err(c, FBSDE_ERR_CUDA, "cuTensorMapEncodeTiled failed (driver entry point or arguments)");
+    return FBSDE_OK;
 }
-void bf16_destroy(fbsde_ctx* ctx) { ctx->bf = nullptr; }
-fbsde_status bf16_prepare_weights(fbsde_ctx* ctx, const float*) { return set_err(ctx, FBSDE_ERR_UNSUPPORTED, "BF16"); }
-fbsde_status bf16_forward(fbsde_ctx* ctx, const float*) { return set_err(ctx, FBSDE_ERR_UNSUPPORTED, "BF16"); }
-fbsde_status bf16_backward(fbsde_ctx* ctx, const float*, float*) { return set_err(ctx, FBSDE_ERR_UNSUPPORTED, "BF16"); }
+
+void bf16_destroy(fbsde_ctx* c) {
+    if (!c->bf) return;
+    if (c->bf->mem) cudaFree(c->bf->mem);
+    delete c->bf;
+    c->bf = nullptr;
+}
+
+// ------------------------------------------------------------------ activations
+
+// act and its first two derivatives with fast SFU math (BF16 form).  tanh
+// from e = exp(-2|a|): tanh = sign(a) (1 - e) / (1 + e), tanh' = 4 e / (1 + e)^2
+// (no cancellation where tanh saturates), tanh'' = -2 tanh tanh'.
+__device__ __forceinline__ Act3 act3_fast(int act, float a) {
+    Act3 r;
+    if (act == FBSDE_SIN) {
+        float s, c;
+        __sincosf(a, &s, &c);
+        r.f = s; r.d1 = c; r.d2 = -s;
+    } else {
+        const float e = __expf(-2.f * fabsf(a));
+        const float q = __fdividef(1.f, 1.f + e);
+        const float t = copysignf((1.f - e) * q, a);
+        r.f = t; r.d1 = 4.f * e * q * q; r.d2 = -2.f * t * r.d1;
+    }
+    return r;
+}
+
+__device__ __forceinline__ void ld16f(const float* p, float (&v)[16]) {
+    const float4* q = reinterpret_cast<const float4*>(p);
+#pragma unroll
+    for (int i = 0; i < 4; ++i) {
+        float4 x = __ldg(q + i);
+        v[4 * i] = x.x; v[4 * i + 1] = x.y; v[4 * i + 2] = x.z; v[4 * i + 3] = x.w;
+    }
+}
+__device__ __forceinline__ void st16f(float* p, const float (&v)[16]) {
+    float4* q = reinterpret_cast<float4*>(p);
+#pragma unroll
+    for (int i = 0; i < 4; ++i) q[i] = make_float4(v[4 * i], v[4 * i + 1], v[4 * i + 2], v[4 * i + 3]);
+}
+__device__ __forceinline__ void st16b(bf16* p, const float (&v)[16]) {
+    uint4 u[2];
+    uint32_t* w = reinterpret_cast<uint32_t*>(u);
+#pragma unroll
+    for (int i = 0; i < 8; ++i) {
+        __nv_bfloat162 h = __floats2bfloat162_rn(v[2 * i], v[2 * i + 1]);
+        w[i] = *reinterpret_cast<uint32_t*>(&h);
+    }
+    uint4* q = reinterpret_cast<uint4*>(p);
+    q[0] = u[0];
+    q[1] = u[1];
+}
+
+// ------------------------------------------------------------------ epilogues (16 columns per call)
+
+struct EpiFwdB {  // a = acc + b + t tcol; h = s hprev + c act(a)
+    const float* bias; const float* tcol; int K0; const float* hprev; float s, c;
+    float* aout; float* hout; bf16* hbout; int w, wp, M; float dt; int act;
+    __device__ void operator()(int row, int c0, const float (&v)[16], int) const {
+        const float t = (float)(row / M) * dt;
+        float a[16], h[16], hp[16];
+        if (hprev) ld16f(hprev + (size_t)row * w + c0, hp);
+#pragma unroll
+        for (int j = 0; j < 16; ++j) {
+            a[j] = v[j] + bias[c0 + j];
+            if (tcol) a[j] += t * tcol[(size_t)(c0 + j) * K0];
+            const float f = act3_fast(act, a[j]).f;
+            h[j] = (hprev ? s * hp[j] : 0.f) + c * f;
+        }
+        st16f(aout + (size_t)row * w + c0, a);
+        st16f(hout + (size_t)row * w + c0, h);
+        st16b(hbout + (size_t)row * wp + c0, h);
+    }
+};
+
+struct EpiRevB {  // g = s g_l + acc; e = c_prev act'(a_prev) g
+    const float* gl; float s; const float* aprev; float cprev;
+    float* gout; bf16* eout; int w, wp; int act;
+    __device__ void operator()(int row, int c0, const float (&v)[16], int) const {
+        float g[16], e[16], gv[16], ap[16];
+        ld16f(gl + (size_t)row * w + c0, gv);
+        ld16f(aprev + (size_t)row * w + c0, ap);
+#pragma unroll
+        for (int j = 0; j < 16; ++j) {
+            g[j] = s * gv[j] + v[j];
+            e[j] = cprev * act3_fast(act, ap[j]).d1 * g[j];
+        }
+        st16f(gout + (size_t)row * w + c0, g);
+        st16b(eout + (size_t)row * wp + c0, e);
+    }
+};
+
+struct EpiZB {  // Z (+)= acc, columns < D
+    float* Z; int D; int accumulate;
+    __device__ void operator()(int row, int c0, const float (&v)[16], int) const {
+        float* z = Z + (size_t)row * D;
+#pragma unroll
+        for (int j = 0; j < 16; ++j)
+            if (c0 + j < D) z[c0 + j] = accumulate ? z[c0 + j] + v[j] : v[j];
+    }
+};
+
+struct EpiTanB {  // h' = s h'_prev + c act'(a) a'; S = c act''(a) a' g
+    const float* a; const float* hdprev; const float* g; float s, c;
+    float* hdout; bf16* hdbout; float* sout; int w, wp; int act;
+    __device__ void operator()(int row, int c0, const float (&v)[16], int) const {
+        float av[16], gv[16], hp[16], hd[16], sv[16];
+        const size_t o = (size_t)row * w + c0;
+        ld16f(a + o, av);
+        ld16f(g + o, gv);
+        if (hdprev) ld16f(hdprev + o, hp);
+#pragma unroll
+        for (int j = 0; j < 16; ++j) {
+            const Act3 f = act3_fast(act, av[j]);
+            hd[j] = (hdprev ? s * hp[j] : 0.f) + c * f.d1 * v[j];
+            sv[j] = c * f.d2 * v[j] * gv[j];
+        }
+        st16f(hdout + o, hd);
+        st16b(hdbout + (size_t)row * wp + c0, hd);
+        st16f(sout + o, sv);
+    }
+};
+
+struct EpiAdjB {  // hbar = s hbar_l + acc; abar_prev = c_prev act'(a_prev) hbar + S_prev
+    const float* hbl; float s; const float* aprev; const float* sprev; float cprev;
+    float* hbout; bf16* about; int w, wp; int act;
+    __device__ void operator()(int row, int c0, const float (&v)[16], int) const {
+        float hv[16], ap[16], sp[16], hb[16], ab[16];
+        const size_t o = (size_t)row * w + c0;
+        ld16f(hbl + o, hv);
+        ld16f(aprev + o, ap);
+        ld16f(sprev + o, sp);
+#pragma unroll
+        for (int j = 0; j < 16; ++j) {
+            hb[j] = s * hv[j] + v[j];
+            ab[j] = cprev * act3_fast(act, ap[j]).d1 * hb[j] + sp[j];
+        }
+        st16f(hbout + o, hb);
+        st16b(about + (size_t)row * wp + c0, ab);
+    }
+};
+
+struct EpiPartB {  // split-K partial sums part[split][row][col]
+    float* part; int rows, N;
+    __device__ void operator()(int row, int c0, const float (&v)[16], int split) const {
+        st16f(part + ((size_t)split * rows + row) * N + c0, v);
+    }
+};
+
+struct EpiStoreB {  // C[row][c0 + j] = acc for columns < N
+    float* C; int ldc, N;
+    __device__ void operator()(int row, int c0, const float (&v)[16], int) const {
+#pragma unroll
+        for (int j = 0; j < 16; ++j)
+            if (c0 + j < N) C[(size_t)row * ldc + c0 + j] = v[j];
+    }
+};
+
+// ------------------------------------------------------------------ small kernels
+
+// out[r][c] (row stride ldo, zero padded to rows_o x cols_o) = src(r, c) with
+// src(r, c) = S[r * lds + off + c] (or S[c * lds + off + r] when transposed)
+// for r < rows_v, c < cols_v.
+__global__ void k_cvt_bf16(int rows_o, int cols_o, int ldo, bf16* __restrict__ out, const float* __restrict__ S,
+                           int lds, int off, int rows_v, int cols_v, int transpose) {
+    const size_t i = (size_t)blockIdx.x * blockDim.x + threadIdx.x;
+    if (i >= (size_t)rows_o * cols_o) return;
+    const int r = (int)(i / cols_o), cc = (int)(i % cols_o);
+    float x = 0.f;
+    if (r < rows_v && cc < cols_v) x = transpose ? S[(size_t)cc * lds + off + r] : S[(size_t)r * lds + off + cc];
+    out[(size_t)r * ldo + cc] = __float2bfloat16_rn(x);
+}
+
+// g_L = w_o, e_L = c_L act'(a_L) w_o (BF16)
+__global__ void k_top_rev_b(size_t P, int w, int wp, const float* __restrict__ aL, const float* __restrict__ wo,
+                            float cL, int act, float* __restrict__ gL, bf16* __restrict__ eL) {
+    const size_t i = (size_t)blockIdx.x * blockDim.x + threadIdx.x;
+    if (i >= P * w) return;
+    const size_t p = i / w;
+    const int j = (int)(i % w);
+    gL[i] = wo[j];
+    eL[p * wp + j] = __float2bfloat16_rn(cL * act3_fast(act, aL[i]).d1 * wo[j]);
+}
+
+// hbar_L = alpha w_o, abar_L = c_L act'(a_L) hbar_L + S_L (BF16)
+__global__ void k_top_adj_b(size_t P, int w, int wp, const float* __restrict__ aL, const float* __restrict__ wo,
+                            const float* __restrict__ alpha, const float* __restrict__ SL, float cL, int act,
+                            float* __restrict__ hbL, bf16* __restrict__ abL) {
+    const size_t i = (size_t)blockIdx.x * blockDim.x + threadIdx.x;
+    if (i >= P * w) return;
+    const size_t p = i / w;
+    const int j = (int)(i % w);
+    const float hb = alpha[p] * wo[j];
+    hbL[i] = hb;
+    abL[p * wp + j] = __float2bfloat16_rn(cL * act3_fast(act, aL[i]).d1 * hb + SL[i]);
+}
+
+// Partial column sums over a range of points, fixed order:
+// part[split][c] = sum_{p in split} wt(p) X[p][c], wt = 1 (mode 0), t_p (mode 1)
+// or wts[p] (mode 2).
+template <class T>
+__global__ void k_colsum(size_t P, int ncols, const T* __restrict__ X, int ldx, int mode,
+                         const float* __restrict__ wts, int M, float dt, float* __restrict__ part, size_t chunk) {
+    const int c = blockIdx.x * blockDim.x + threadIdx.x;
+    const int split = blockIdx.y;
+    if (c >= ncols) return;
+    const size_t p0 = (size_t)split * chunk, p1 = min(P, p0 + chunk);
+    float s = 0.f;
+    for (size_t p = p0; p < p1; ++p) {
+        const float wt = mode == 0 ? 1.f : mode == 1 ? (float)(p / M) * dt : wts[p];
+        s = fmaf(wt, (float)X[p * ldx + c], s);
+    }
+    part[(size_t)split * ncols + c] = s;
+}
+
+__global__ void k_colsum_reduce(const float* __restrict__ part, int splits, int ncols, float* __restrict__ out,
+                                int ldo, int accumulate) {
+    const int c = blockIdx.x * blockDim.x + threadIdx.x;
+    if (c >= ncols) return;
+    float s = 0.f;
+    for (int k = 0; k < splits; ++k) s += part[(size_t)k * ncols + c];
+    out[(size_t)c * ldo] = accumulate ? out[(size_t)c * ldo] + s : s;
+}
+
+// out[r * ld + off + c] = sum_z part[z][r][c] for c < nc (fixed order)
+__global__ void k_reduce_split(const float* __restrict__ part, int splits, int rows, int N, int nc,
+                               float* __restrict__ out, int ld, int off) {
+    const int i = blockIdx.x * blockDim.x + threadIdx.x;
+    if (i >= rows * nc) return;
+    const int r = i / nc, cc = i % nc;
+    float s = 0.f;
+    for (int z = 0; z < splits; ++z) s += part[((size_t)z * rows + r) * N + cc];
+    out[(size_t)r * ld + off + cc] = s;
+}
+
+// ------------------------------------------------------------------ launch helpers
+
+template <bool TN, class Epi>
+static fbsde_status tc_launch(fbsde_ctx* c, int cls, const TcArgs& a, int splits, const Epi& e, double flops) {
+    const int tok = prof_begin(c, cls);
+    cudaError_t err = tc_gemm<TN>(a, splits, e, c->stream);
+    prof_end(c, cls, tok, flops);
+    if (err != cudaSuccess) return set_err(c, FBSDE_ERR_CUDA, std::string("tcgen05 GEMM: ") + cudaGetErrorString(err));
+    ++c->n_launch;
+    return FBSDE_OK;
+}
+
+static TcArgs nt_args(fbsde_ctx* c, int rows, int N) {
+    TcArgs a;
+    std::memset(&a, 0, sizeof(a));
+    a.rows = rows; a.N = N; a.kchunk = 0; a.err = c->bf->err;
+    return a;
+}
+static void add_pair(TcArgs& a, const CUtensorMap& A, const CUtensorMap& B, int K) {
+    a.pr[a.npairs].a = A;
+    a.pr[a.npairs].b = B;
+    a.pr[a.npairs].K = K;
+    ++a.npairs;
+}
+
+static fbsde_status colsum(fbsde_ctx* c, int cls, const void* X, bool is_bf16, int ldx, int ncols, int mode,
+                           const float* wts, float* out, int ldo, int accumulate) {
+    Bf16Work* b = c->bf;
+    const size_t P = c->P();
+    const size_t chunk = (P + kColSplits - 1) / kColSplits;
+    const int splits = (int)((P + chunk - 1) / chunk);
+    const float dt = (float)(c->T / c->N);
+    dim3 grid(nblk(ncols, 128), splits);
+    const int tok = prof_begin(c, cls);
+    if (is_bf16)
+        k_colsum<bf16><<<grid, 128, 0, c->stream>>>(P, ncols, (const bf16*)X, ldx, mode, wts, c->M, dt, b->colpart, chunk);
+    else
+        k_colsum<float><<<grid, 128, 0, c->stream>>>(P, ncols, (const float*)X, ldx, mode, wts, c->M, dt, b->colpart, chunk);
+    FBSDE_CK_LAUNCH(c);
+    k_colsum_reduce<<<nblk(ncols, 128), 128, 0, c->stream>>>(b->colpart, splits, ncols, out, ldo, accumulate);
+    prof_end(c, cls, tok, 2.0 * (double)P * ncols);
+    FBSDE_CK_LAUNCH(c);
+    return FBSDE_OK;
+}
+
+// Weight gradient: out[r * ld + off + j] = sum over points of the TN pairs,
+// for output rows r < rows and columns j < ncols_store.
+static fbsde_status wgrad(fbsde_ctx* c, TcArgs a, int ncols_store, float* out, int ld, int off) {
+    const size_t P = c->P();
+    const int mblocks = (a.rows + 127) / 128;
+    int want = (2 * 148 + mblocks - 1) / mblocks;
+    size_t kc = rup((P + want - 1) / want, 64);
+    int splits = (int)((P + kc - 1) / kc);
+    while ((size_t)splits * a.rows * a.N > c->part_floats) {
+        kc *= 2;
+        splits = (int)((P + kc - 1) / kc);
+    }
+    a.kchunk = (int)kc;
+    double flops = 0;
+    for (int q = 0; q < a.npairs; ++q) flops += 2.0 * a.rows * (double)ncols_store * P;
+    FBSDE_TRY(tc_launch<true>(c, PROF_WGRAD, a, splits, EpiPartB{c->part, a.rows, a.N}, flops));
+    k_reduce_split<<<nblk((size_t)a.rows * ncols_store, 256), 256, 0, c->stream>>>(c->part, splits, a.rows, a.N,
+                                                                                   ncols_store, out, ld, off);
+    FBSDE_CK_LAUNCH(c);
+    return FBSDE_OK;
+}
+
+// ------------------------------------------------------------------ weights
+
+fbsde_status bf16_prepare_weights(fbsde_ctx* c, const float* theta) {
+    FBSDE_TRY(fp32_prepare_weights(c, theta));  // NAIS: A_l = -R^T R - eps I in FP32
+    Bf16Work* b = c->bf;
+    const int w = c->w, D = c->D, K0 = D + 1;
+    const ParamLayout& pl = c->pl;
+    auto cvt = [&](bf16* out, int rows_o, int cols_o, int ldo, const float* S, int lds, int off, int rows_v,
+                   int cols_v, int tr) -> fbsde_status {
+        k_cvt_bf16<<<nblk((size_t)rows_o * cols_o, 256), 256, 0, c->stream>>>(rows_o, cols_o, ldo, out, S, lds, off,
+                                                                             rows_v, cols_v, tr);
+        FBSDE_CK_LAUNCH(c);
+        return FBSDE_OK;
+    };
+    FBSDE_TRY(cvt(b->Winx, w, b->Dp, b->Dp, theta + pl.Win, K0, 1, w, D, 0));
+    FBSDE_TRY(cvt(b->WinxT, b->Dn, b->wp, b->wp, theta + pl.Win, K0, 1, D, w, 1));
+    for (int l = 1; l <= c->L; ++l) {
+        const float* Wm = c->akind == FBSDE_NAIS ? c->Amat[l] : theta + pl.W[l];
+        FBSDE_TRY(cvt(b->W[l], w, b->wp, b->wp, Wm, w, 0, w, w, 0));
+        FBSDE_TRY(cvt(b->WT[l], w, b->wp, b->wp, Wm, w, 0, w, w, 1));
+        if (c->akind == FBSDE_NAIS) {
+            FBSDE_TRY(cvt(b->Bx[l], w, b->Dp, b->Dp, theta + pl.B[l], K0, 1, w, D, 0));
+            FBSDE_TRY(cvt(b->BxT[l], b->Dn, b->wp, b->wp, theta + pl.B[l], K0, 1, D, w, 1));
+        }
+    }
+    return FBSDE_OK;
+}
+
+// ------------------------------------------------------------------ forward
+
+fbsde_status bf16_forward(fbsde_ctx* c, const float* theta) {
+    Bf16Work* b = c->bf;
+    const int w = c->w, L = c->L, D = c->D, K0 = D + 1, act = c->act, wp = b->wp;
+    const int P = (int)c->P();
+    const ParamLayout& pl = c->pl;
+    const float dt = (float)(c->T / c->N);
+    const bool nais = c->akind == FBSDE_NAIS;
+    cudaStream_t st = c->stream;
+
+    // GEMM operand copy of X
+    k_cvt_bf16<<<nblk((size_t)P * b->Dp, 256), 256, 0, st>>>(P, b->Dp, b->Dp, b->Xb, c->X, D, 0, P, D, 0);
+    FBSDE_CK_LAUNCH(c);
+
+    {   // lift
+        TcArgs a = nt_args(c, P, w);
+        add_pair(a, b->mXb, b->mWinx, D);
+        EpiFwdB e{theta + pl.bin, theta + pl.Win, K0, nullptr, 0.f, 1.f, b->Af[0], b->Hf[0], b->Hb[0], w, wp,
+                  c->M, dt, act};
+        FBSDE_TRY(tc_launch<false>(c, PROF_POINTS, a, 1, e, 2.0 * P * w * (double)D));
+    }
+    for (int l = 1; l <= L; ++l) {
+        TcArgs a = nt_args(c, P, w);
+        add_pair(a, b->mHb[l - 1], b->mW[l], w);
+        double fl = 2.0 * P * w * (double)w;
+        if (nais) { add_pair(a, b->mXb, b->mBx[l], D); fl += 2.0 * P * w * (double)D; }
+        EpiFwdB e{theta + pl.b[l], nais ? theta + pl.B[l] : nullptr, K0, b->Hf[l - 1], layer_skip(c, l),
+                  layer_scale(c, l), b->Af[l], b->Hf[l], b->Hb[l], w, wp, c->M, dt, act};
+        FBSDE_TRY(tc_launch<false>(c, PROF_POINTS, a, 1, e, fl));
+    }
+    FBSDE_TRY(launch_rowdot(c, b->Hf[L], theta, c->Y));
+
+    k_top_rev_b<<<nblk((size_t)P * w, 256), 256, 0, st>>>(P, w, wp, b->Af[L], theta + pl.wo, layer_scale(c, L), act,
+                                                          b->Gf[L], b->Eb[L]);
+    FBSDE_CK_LAUNCH(c);
+    for (int l = L; l >= 1; --l) {
+        TcArgs a = nt_args(c, P, w);
+        add_pair(a, b->mEb[l], b->mWT[l], w);
+        EpiRevB e{b->Gf[l], layer_skip(c, l), b->Af[l - 1], layer_scale(c, l - 1), b->Gf[l - 1], b->Eb[l - 1], w, wp,
+                  act};
+        FBSDE_TRY(tc_launch<false>(c, PROF_POINTS, a, 1, e, 2.0 * P * w * (double)w));
+    }
+    {   // Z = W_in[:,1:]^T e_0 (+ sum_l B_l[:,1:]^T e_l)
+        TcArgs a = nt_args(c, P, b->Dn);
+        add_pair(a, b->mEb[0], b->mWinxT, w);
+        FBSDE_TRY(tc_launch<false>(c, PROF_POINTS, a, 1, EpiZB{c->Z, D, 0}, 2.0 * P * D * (double)w));
+        if (nais) {
+            for (int l = 1; l <= L; ++l) {
+                TcArgs an = nt_args(c, P, b->Dn);
+                add_pair(an, b->mEb[l], b->mBxT[l], w);
+                FBSDE_TRY(tc_launch<false>(c, PROF_POINTS, an, 1, EpiZB{c->Z, D, 1}, 2.0 * P * D * (double)w));
+            }
+        }
+    }
+    return FBSDE_OK;
+}
+
+// ------------------------------------------------------------------ backward
+
+fbsde_status bf16_backward(fbsde_ctx* c, const float* theta, float* grad) {
+    Bf16Work* b = c->bf;
+    const int w = c->w, L = c->L, D = c->D, K0 = D + 1, act = c->act, wp = b->wp;
+    const int P = (int)c->P();
+    const ParamLayout& pl = c->pl;
+    const bool nais = c->akind == FBSDE_NAIS;
+    cudaStream_t st = c->stream;
+
+    k_cvt_bf16<<<nblk((size_t)P * b->Dp, 256), 256, 0, st>>>(P, b->Dp, b->Dp, b->Vb, c->V, D, 0, P, D, 0);
+    FBSDE_CK_LAUNCH(c);
+
+    {   // tangent lift along u' = (0, v)
+        TcArgs a = nt_args(c, P, w);
+        add_pair(a, b->mVb, b->mWinx, D);
+        EpiTanB e{b->Af[0], nullptr, b->Gf[0], 0.f, 1.f, b->HDf[0], b->HDb[0], b->Sf[0], w, wp, act};
+        FBSDE_TRY(tc_launch<false>(c, PROF_POINTS, a, 1, e, 2.0 * P * w * (double)D));
+    }
+    for (int l = 1; l <= L; ++l) {
+        TcArgs a = nt_args(c, P, w);
+        add_pair(a, b->mHDb[l - 1], b->mW[l], w);
+        double fl = 2.0 * P * w * (double)w;
+        if (nais) { add_pair(a, b->mVb, b->mBx[l], D); fl += 2.0 * P * w * (double)D; }
+        EpiTanB e{b->Af[l], b->HDf[l - 1], b->Gf[l], layer_skip(c, l), layer_scale(c, l), b->HDf[l], b->HDb[l],
+                  b->Sf[l], w, wp, act};
+        FBSDE_TRY(tc_launch<false>(c, PROF_POINTS, a, 1, e, fl));
+    }
+    k_top_adj_b<<<nblk((size_t)P * w, 256), 256, 0, st>>>(P, w, wp, b->Af[L], theta + pl.wo, c->alpha, b->Sf[L],
+                                                          layer_scale(c, L), act, b->HBf[L], b->ABb[L]);
+    FBSDE_CK_LAUNCH(c);
+    for (int l = L; l >= 1; --l) {
+        TcArgs a = nt_args(c, P, w);
+        add_pair(a, b->mABb[l], b->mWT[l], w);
+        EpiAdjB e{b->HBf[l], layer_skip(c, l), b->Af[l - 1], b->Sf[l - 1], layer_scale(c, l - 1), b->HBf[l - 1],
+                  b->ABb[l - 1], w, wp, act};
+        FBSDE_TRY(tc_launch<false>(c, PROF_POINTS, a, 1, e, 2.0 * P * w * (double)w));
+    }
+
+    // weight gradients: contractions over all points on the tensor cores
+    for (int l = 1; l <= L; ++l) {
+        TcArgs a = nt_args(c, w, w);
+        add_pair(a, b->tAB[l], b->tH[l - 1], P);
+        add_pair(a, b->tE[l], b->tHD[l - 1], P);
+        FBSDE_TRY(wgrad(c, a, w, nais ? c->gA[l] : grad + pl.W[l], w, 0));
+        FBSDE_TRY(colsum(c, PROF_WGRAD, b->ABb[l], true, wp, w, 0, nullptr, grad + pl.b[l], 1, 0));
+        if (nais) {
+            FBSDE_TRY(colsum(c, PROF_WGRAD, b->ABb[l], true, wp, w, 1, nullptr, grad + pl.B[l], K0, 0));
+            TcArgs ax = nt_args(c, w, b->Dn);
+            add_pair(ax, b->tAB[l], b->tX, P);
+            add_pair(ax, b->tE[l], b->tV, P);
+            FBSDE_TRY(wgrad(c, ax, D, grad + pl.B[l], K0, 1));
+            FBSDE_TRY(nais_chain_R(c, theta, grad, l));
+        }
+    }
+    {
+        TcArgs ax = nt_args(c, w, b->Dn);
+        add_pair(ax, b->tAB[0], b->tX, P);
+        add_pair(ax, b->tE[0], b->tV, P);
+        FBSDE_TRY(wgrad(c, ax, D, grad + pl.Win, K0, 1));
+        FBSDE_TRY(colsum(c, PROF_WGRAD, b->ABb[0], true, wp, w, 0, nullptr, grad + pl.bin, 1, 0));
+        FBSDE_TRY(colsum(c, PROF_WGRAD, b->ABb[0], true, wp, w, 1, nullptr, grad + pl.Win, K0, 0));
+    }
+    // dw_o = sum_p alpha_p h_L(p) + h'_L(p);  db_o = sum_p alpha_p
+    FBSDE_TRY(colsum(c, PROF_WGRAD, b->Hf[L], false, w, w, 2, c->alpha, grad + pl.wo, 1, 0));
+    FBSDE_TRY(colsum(c, PROF_WGRAD, b->HDf[L], false, w, w, 0, nullptr, grad + pl.wo, 1, 1));
+    FBSDE_TRY(colsum(c, PROF_WGRAD, c->alpha, false, 1, 1, 0, nullptr, grad + pl.bo, 1, 0));
+    return launch_check_finite(c, grad, pl.total);
+}
 
 }  // namespace fbsde
+
+// ------------------------------------------------------------------ C ABI: the contraction engine
+
+using namespace fbsde;
+
+extern "C" fbsde_status fbsde_gemm_bf16(const void* A_dev, const void* B_dev, float* C_dev, int rows, int N, int K,
+                                        int lda, int ldb, int ldc, int trans, void* cuda_stream) {
+    if (!A_dev || !B_dev || !C_dev) return FBSDE_ERR_INVALID;
+    if (rows < 1 || K < 1 || N < 16 || N > 256 || N % 16 != 0 || ldc < N) return FBSDE_ERR_INVALID;
+    if (lda % 8 != 0 || ldb % 8 != 0 || ((uintptr_t)A_dev & 15) || ((uintptr_t)B_dev & 15)) return FBSDE_ERR_INVALID;
+    if (trans != 0 && trans != 1) return FBSDE_ERR_INVALID;
+    if (trans == 0 && (lda < K || ldb < K)) return FBSDE_ERR_INVALID;
+    if (trans == 1 && (lda < rows || ldb < N)) return FBSDE_ERR_INVALID;
+    cudaStream_t st = (cudaStream_t)cuda_stream;
+    TcArgs a;
+    std::memset(&a, 0, sizeof(a));
+    a.rows = rows; a.N = N; a.npairs = 1; a.err = nullptr; a.pr[0].K = K;
+    bool ok;
+    if (trans == 0) {
+        ok = map2d(&a.pr[0].a, A_dev, (uint64_t)K, (uint64_t)rows, (uint64_t)lda, 128) &&
+             map2d(&a.pr[0].b, B_dev, (uint64_t)K, (uint64_t)N, (uint64_t)ldb, (uint32_t)N);
+    } else {
+        ok = map2d(&a.pr[0].a, A_dev, (uint64_t)rows, (uint64_t)K, (uint64_t)lda, 64) &&
+             map2d(&a.pr[0].b, B_dev, (uint64_t)N, (uint64_t)K, (uint64_t)ldb, 64);
+        a.kchunk = (int)rup((size_t)K, 64);
+    }
+    if (!ok) return FBSDE_ERR_CUDA;
+    cudaError_t e = trans == 0 ? tc_gemm<false>(a, 1, EpiStoreB{C_dev, ldc, N}, st)
+                               : tc_gemm<true>(a, 1, EpiStoreB{C_dev, ldc, N}, st);
+    if (e == cudaSuccess) e = cudaStreamSynchronize(st);
+    return e == cudaSuccess ? FBSDE_OK : FBSDE_ERR_CUDA;
+}

@@ -105,32 +105,44 @@ def _check_eval(P, prob, arch, seed=3, it=11, perturb=0.1, tol=None):
     return errs
 
 
-def test_small_workload_fp32(P):
-    w = P.workloads.WORKLOADS["bsb_d10_n8_m64_fc4x64_sin"]
+@pytest.mark.parametrize("prec", ["fp32", "bf16"])
+def test_small_workload(P, prec):
+    w = P.workloads.WORKLOADS["bsb_d10_n8_m64_fc4x64_sin"].with_prec(prec)
     _check_eval(P, w.problem, w.arch, seed=w.seed, perturb=0.0)
 
 
+@pytest.mark.parametrize("prec", ["fp32", "bf16"])
 @pytest.mark.parametrize("kind", ["fc", "resnet", "nais"])
 @pytest.mark.parametrize("pk", ["bsb", "hjb"])
 @pytest.mark.parametrize("act", ["sin", "tanh"])
-def test_arch_problem_grid_fp32(P, kind, pk, act):
+def test_arch_problem_grid(P, kind, pk, act, prec):
     D = 6
     x0 = [1.0, 0.5] * 3 if pk == "bsb" else [0.0] * D
     prob = P.ProblemSpec(kind=pk, D=D, N=5, M=24, x0=x0, terminal_grad_term=(kind == "resnet"))
-    arch = P.ArchSpec(kind=kind, width=32, depth=3, act=act, h=0.5 if kind == "nais" else 1.0)
+    arch = P.ArchSpec(kind=kind, width=32, depth=3, act=act, h=0.5 if kind == "nais" else 1.0, prec=prec)
     _check_eval(P, prob, arch)
 
 
-def test_ragged_tiles_fp32(P):
+@pytest.mark.parametrize("prec", ["fp32", "bf16"])
+def test_ragged_tiles(P, prec):
     # P = 37 * 8 = 296 points (two full 128-row tiles and a tail), width 48
-    # (a partial 128-column tile), D = 13 (not a multiple of 4).
+    # (a partial column tile), D = 13 (not a multiple of 4).
     prob = P.ProblemSpec(kind="bsb", D=13, N=7, M=37, x0=[0.7] * 13)
-    arch = P.ArchSpec(kind="resnet", width=48, depth=2, act="tanh")
+    arch = P.ArchSpec(kind="resnet", width=48, depth=2, act="tanh", prec=prec)
     _check_eval(P, prob, arch)
 
 
+@pytest.mark.parametrize("prec", ["fp32", "bf16"])
+def test_multi_tile_width256(P, prec):
+    # several 128-point tiles at the measured width: P = 9 * 65 = 585
+    prob = P.ProblemSpec(kind="bsb", D=100, N=64, M=9, x0=P.workloads.bsb_x0(100))
+    arch = P.ArchSpec(kind="resnet", width=256, depth=5, act="tanh", prec=prec)
+    _check_eval(P, prob, arch, perturb=0.0)
+
+
+@pytest.mark.parametrize("prec", ["fp32", "bf16"])
 @pytest.mark.parametrize("case", ["D1_N1_M1", "depth0", "M1"])
-def test_edge_cases_fp32(P, case):
+def test_edge_cases(P, case, prec):
     if case == "D1_N1_M1":
         prob = P.ProblemSpec(kind="hjb", D=1, N=1, M=1, x0=[0.3])
         arch = P.ArchSpec(kind="fc", width=16, depth=1, act="sin")
@@ -140,6 +152,7 @@ def test_edge_cases_fp32(P, case):
     else:
         prob = P.ProblemSpec(kind="bsb", D=8, N=16, M=1, x0=[1.0, 0.5] * 4)
         arch = P.ArchSpec(kind="nais", width=16, depth=2, act="tanh")
+    arch.prec = prec
     _check_eval(P, prob, arch)
 
 
