@@ -224,6 +224,30 @@ fbsde_status fbsde_profile_read(fbsde_ctx* ctx, int cls, double* ms_total, uint6
 /* Kernels launched by this context since it was created. */
 uint64_t fbsde_launch_count(const fbsde_ctx* ctx);
 
+/* The residual, loss-seed and loss step (what fbsde_rollout_loss does after
+ * the network pass) for callers that cannot allocate device memory, e.g. an
+ * application whose own pool owns all device memory, or a loop that cannot
+ * afford an allocation's implicit synchronisation.  The paper has no
+ * counterpart: this is a deployment variant of the same step.
+ * Inputs, in the layouts of fbsde_sample_paths and fbsde_rollout_detail:
+ * X_dev [(N+1) M D], dW_dev [N M D], Y_dev [(N+1) M], Z_dev [(N+1) M D].
+ * Outputs: alpha_dev [(N+1) M] = d loss / d Y_n, V_dev [(N+1) M D] =
+ * d loss / d Z_n, loss_dev and y0_dev (one float each), as fbsde_rollout_loss.
+ * No allocation: the per-path FP64 loss terms go to a fixed device array of
+ * 65536 doubles (512 KiB, reserved on every GPU that loads the library until
+ * the process exits), so M must be <= 65536 (FBSDE_ERR_INVALID otherwise,
+ * with the reason in err_msg_host if non-NULL, 256 bytes).  Each call writes
+ * all M terms before summing them, so nothing has to start at zero, but every
+ * call on a device uses the same array: calls whose work overlaps on the GPU
+ * (other streams, other threads) race and must be serialised by the caller.
+ * The first call on a device looks up the array's device address once (with
+ * that device current); make that first call before any stream capture.
+ * Work is enqueued on `cuda_stream`; no host synchronisation. */
+fbsde_status fbsde_residual_loss_noalloc(const fbsde_problem* problem, const float* X_dev,
+                                         const float* dW_dev, const float* Y_dev, const float* Z_dev,
+                                         float* alpha_dev, float* V_dev, float* loss_dev, float* y0_dev,
+                                         void* cuda_stream, char* err_msg_host);
+
 const char* fbsde_status_string(fbsde_status s);
 const char* fbsde_last_error(const fbsde_ctx* ctx);
 

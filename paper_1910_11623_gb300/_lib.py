@@ -57,6 +57,8 @@ SIGNATURES = {
     "fbsde_profile_read": (c_int, [c_void_p, c_int, POINTER(c_double), POINTER(c_uint64),
                                    POINTER(c_double)]),
     "fbsde_launch_count": (c_uint64, [c_void_p]),
+    "fbsde_residual_loss_noalloc": (c_int, [POINTER(fbsde_problem), c_void_p, c_void_p, c_void_p, c_void_p,
+                                            c_void_p, c_void_p, c_void_p, c_void_p, c_void_p, c_char_p]),
     "fbsde_status_string": (c_char_p, [c_int]),
     "fbsde_last_error": (c_char_p, [c_void_p]),
 }
@@ -200,6 +202,19 @@ def fbsde_profile_read(ctx, cls: int):
 
 def fbsde_launch_count(ctx) -> int:
     return int(load().fbsde_launch_count(ctx))
+
+
+def fbsde_residual_loss_noalloc(problem: fbsde_problem, X_ptr: int, dW_ptr: int, Y_ptr: int, Z_ptr: int,
+                                alpha_ptr: int, V_ptr: int, loss_ptr: int, y0_ptr: int, stream: int):
+    """Residuals, seeds and loss from caller-held paths and network values,
+    without any device allocation (scratch in a fixed device array, M <= 65536)."""
+    msg = ctypes.create_string_buffer(256)
+    s = load().fbsde_residual_loss_noalloc(ctypes.byref(problem), c_void_p(X_ptr), c_void_p(dW_ptr),
+                                           c_void_p(Y_ptr), c_void_p(Z_ptr), c_void_p(alpha_ptr),
+                                           c_void_p(V_ptr), c_void_p(loss_ptr), c_void_p(y0_ptr),
+                                           c_void_p(stream or None), msg)
+    if s != FBSDE_OK:
+        raise FBSDEError(s, "fbsde_residual_loss_noalloc", msg.value.decode())
 
 
 def fbsde_status_string(s: int) -> str:
