@@ -49,6 +49,8 @@ def parse_args():
     ap.add_argument("--cpu-sample-paths", type=int, default=256)
     ap.add_argument("--cpu-iters", type=int, default=3)
     ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--M", type=int, default=0,
+                    help="override the number of paths (small cases for profiler captures)")
     return ap.parse_args()
 
 
@@ -225,6 +227,9 @@ def main():
         torch.cuda.synchronize()
 
     w = P.workloads.WORKLOADS[args.workload].with_prec(args.form)
+    if args.M:
+        from dataclasses import replace as _replace
+        w = _replace(w, problem=_replace(w.problem, M=args.M))
     solver = P.Solver(w.problem, w.arch, seed=w.seed + rank)
     theta = solver.init_params()
     m, v = torch.zeros_like(theta), torch.zeros_like(theta)
