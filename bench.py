@@ -49,6 +49,8 @@ def parse_args():
     ap.add_argument("--cpu-sample-paths", type=int, default=256)
     ap.add_argument("--cpu-iters", type=int, default=3)
     ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--loss-steps", type=int, default=20,
+                    help="timed loss-only evaluations (forward sweep + residuals), 0: skip")
     ap.add_argument("--M", type=int, default=0,
                     help="override the number of paths (small cases for profiler captures)")
     return ap.parse_args()
@@ -317,6 +319,27 @@ def main():
                                for name, p in zip(["points", "wgrad", "other"], prof)},
             "clocks": clk, "e2e": e2e, "gpu_launches": int(launches),
         }
+
+    # loss only (paths, network forward and Z, residuals): the forward half of a step
+    if args.loss_steps > 0:
+        loss_buf, y0_buf = torch.empty(1, device="cuda"), torch.empty(1, device="cuda")
+        for i in range(3):
+            L.fbsde_rollout_loss(solver.ctx, theta.data_ptr(), 10**6 + i, loss_buf.data_ptr(), y0_buf.data_ptr())
+        barrier()
+        L.fbsde_profile_enable(solver.ctx, True)
+        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        e0.record(solver.stream)
+        for i in range(args.loss_steps):
+            L.fbsde_rollout_loss(solver.ctx, theta.data_ptr(), 2 * 10**6 + i, loss_buf.data_ptr(), y0_buf.data_ptr())
+        e1.record(solver.stream)
+        e1.synchronize()
+        pl = L.fbsde_profile_read(solver.ctx, 0)
+        L.fbsde_profile_enable(solver.ctx, False)
+        if out is not None:
+            lms = e0.elapsed_time(e1) / args.loss_steps
+            out["loss_only"] = {"ms_per_eval": lms, "points_ms_per_eval": pl[0] / args.loss_steps,
+                                "points_launches_per_eval": pl[1] / args.loss_steps,
+                                "points_tflops": pl[2] / (pl[0] / 1000.0) / 1e12 if pl[0] > 0 else None}
 
     # FP32 form beside the BF16 form (same workload, same GPU)
     if args.form == "bf16" and args.fp32_steps > 0:

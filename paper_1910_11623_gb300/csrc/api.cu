@@ -238,14 +238,15 @@ fbsde_status fbsde_init_params(fbsde_ctx* ctx, float* theta_dev) {
 namespace fbsde {
 
 // paths -> network values and Z -> residuals, seeds, loss
-static fbsde_status evaluate(fbsde_ctx* c, const float* theta, uint64_t iter, float* loss, float* y0) {
+static fbsde_status evaluate(fbsde_ctx* c, const float* theta, uint64_t iter, float* loss, float* y0,
+                             bool for_grad = false) {
     FBSDE_TRY(launch_paths(c, iter));
     if (c->prec == FBSDE_FP32) {
         FBSDE_TRY(fp32_prepare_weights(c, theta));
         FBSDE_TRY(fp32_forward(c, theta));
     } else {
         FBSDE_TRY(bf16_prepare_weights(c, theta));
-        FBSDE_TRY(bf16_forward(c, theta));
+        FBSDE_TRY(bf16_forward(c, theta, for_grad));
     }
     return launch_seeds(c, loss, y0);
 }
@@ -269,7 +270,7 @@ fbsde_status fbsde_rollout_grad(fbsde_ctx* ctx, const float* theta_dev, uint64_t
                                 float* loss_dev, float* y0_dev, float* grad_dev) {
     if (!ctx || !theta_dev || !grad_dev)
         return set_err(ctx, FBSDE_ERR_INVALID, "ctx, theta_dev and grad_dev must be non-NULL");
-    FBSDE_TRY(evaluate(ctx, theta_dev, iter, loss_dev, y0_dev));
+    FBSDE_TRY(evaluate(ctx, theta_dev, iter, loss_dev, y0_dev, true));
     return gradient(ctx, theta_dev, grad_dev);
 }
 
@@ -280,7 +281,7 @@ fbsde_status fbsde_train_step(fbsde_ctx* ctx, float* theta_dev, float* adam_m_de
     if (step < 1) return set_err(ctx, FBSDE_ERR_INVALID, "step counts Adam steps from 1");
     if (!(lr > 0) || !std::isfinite(lr)) return set_err(ctx, FBSDE_ERR_INVALID, "lr must be finite and > 0");
     float* grad = ctx->gradbuf;
-    FBSDE_TRY(evaluate(ctx, theta_dev, step, loss_dev, y0_dev));
+    FBSDE_TRY(evaluate(ctx, theta_dev, step, loss_dev, y0_dev, true));
     FBSDE_TRY(gradient(ctx, theta_dev, grad));
     FBSDE_TRY(launch_adam(ctx, theta_dev, grad, adam_m_dev, adam_v_dev, step, lr));
     if (ctx->akind == FBSDE_NAIS) FBSDE_TRY(nais_project(ctx, theta_dev));

@@ -1,0 +1,777 @@
+// Per-tile fused kernels of the BF16 form (FC and ResNet networks).
+//
+// Both kernels walk one tile of 128 points (persistent CTAs, one per SM)
+// through a fixed sequence of layer contractions without leaving the SM:
+//   * activation tiles (BF16, 128 rows x up to 256 columns) live in shared
+//     memory in the 128-byte-swizzled K-major layout the tensor cores read,
+//     and each layer's epilogue rewrites them in place;
+//   * the ResNet residual stream (FP32) lives in TMEM columns 256..511 next
+//     to the accumulator (columns 0..255);
+//   * the weights stream from L2 through a TMA ring, one 64-wide K slice per
+//     stage, in the order the layers consume them, so the next layer's
+//     weights arrive while the current epilogue runs;
+//   * per-layer derivatives needed later in the tile go to a per-CTA scratch
+//     region that the same CTA reads back within microseconds.
+// Warp 0 issues the weight TMA loads, warp 1 allocates TMEM and issues
+// tcgen05.mma, warps 2-9 (two groups of four, each group covering the 128
+// TMEM lanes) run the epilogues on alternating 16-column chunks.  The MMA of
+// contraction q+1 starts when all 256 epilogue threads have finished
+// contraction q (mbarrier `aready`): they have read its accumulator and
+// written the operand the next contraction reads.  Every wait is bounded.
+//
+// k_fused_fwdz (Section 2.2: Y = u(t, X) and Z = grad_x u by the reverse
+// pass): lift, L layers, the reverse sweep through the L layers and the Z
+// contraction; outputs Y, Z and g_l (BF16, l < L) for the gradient.
+//
+// k_fused_bwd (the derivative of the loss of Eq. "loss" through Y_n and Z_n):
+// per layer the forward contraction (recomputed) and the tangent contraction
+// along (0, v), then the adjoint sweep down the layers; outputs the operands
+// of the weight-gradient contractions: h_l, h'_l, e_l, abar_l (BF16).
+#include <cuda.h>
+#include <cuda_bf16.h>
+#include <cuda_runtime.h>
+
+#include <cstring>
+#include <string>
+
+#include "bf16_work.cuh"
+#include "tc_common.cuh"
+
+namespace fbsde {
+
+constexpr uint32_t kFStageBytes = 32768;  // one weight slice: up to 256 rows x 128 B
+constexpr uint32_t kFTileBytes = 65536;   // activation tile: 4 x [128 x 64] BF16
+constexpr int kFThreads = 320;
+constexpr int kFEpiThreads = 256;
+constexpr int kFwdStages = 4;
+constexpr int kBwdStages = 2;
+
+struct FGemm {
+    const CUtensorMap* map;
+    int nk, K, N, asel;  // K slices, contraction length, output columns, A tile (0 or 1)
+};
+
+// ---------------------------------------------------------------- small helpers
+
+__device__ __forceinline__ uint32_t pack_bf16x2(float lo, float hi) {
+    __nv_bfloat162 h = __floats2bfloat162_rn(lo, hi);
+    return *reinterpret_cast<uint32_t*>(&h);
+}
+__device__ __forceinline__ float2 unpack_bf16x2(uint32_t u) {
+    return __bfloat1622float2(*reinterpret_cast<const __nv_bfloat162*>(&u));
+}
+
+// Columns col..col+7 (col % 8 == 0) of `row` into / out of a swizzled tile.
+__device__ __forceinline__ void st_tile8(uint8_t* tile, int row, int col, const float* v) {
+    uint4 u;
+    u.x = pack_bf16x2(v[0], v[1]); u.y = pack_bf16x2(v[2], v[3]);
+    u.z = pack_bf16x2(v[4], v[5]); u.w = pack_bf16x2(v[6], v[7]);
+    *reinterpret_cast<uint4*>(tile + (col >> 6) * 16384 + tc::sw128_offset(row, (col & 63) >> 3)) = u;
+}
+__device__ __forceinline__ void ld_tile8(const uint8_t* tile, int row, int col, float* v) {
+    const uint4 u = *reinterpret_cast<const uint4*>(tile + (col >> 6) * 16384 + tc::sw128_offset(row, (col & 63) >> 3));
+    const uint32_t w[4] = {u.x, u.y, u.z, u.w};
+#pragma unroll
+    for (int i = 0; i < 4; ++i) {
+        const float2 f = unpack_bf16x2(w[i]);
+        v[2 * i] = f.x; v[2 * i + 1] = f.y;
+    }
+}
+
+__device__ __forceinline__ void st_bf16x16(bf16* dst, const float* v) {
+    uint4 u0, u1;
+    u0.x = pack_bf16x2(v[0], v[1]);   u0.y = pack_bf16x2(v[2], v[3]);
+    u0.z = pack_bf16x2(v[4], v[5]);   u0.w = pack_bf16x2(v[6], v[7]);
+    u1.x = pack_bf16x2(v[8], v[9]);   u1.y = pack_bf16x2(v[10], v[11]);
+    u1.z = pack_bf16x2(v[12], v[13]); u1.w = pack_bf16x2(v[14], v[15]);
+    reinterpret_cast<uint4*>(dst)[0] = u0;
+    reinterpret_cast<uint4*>(dst)[1] = u1;
+}
+__device__ __forceinline__ void ld_bf16x16(const bf16* src, float* v) {
+    const uint4 u0 = reinterpret_cast<const uint4*>(src)[0];
+    const uint4 u1 = reinterpret_cast<const uint4*>(src)[1];
+    const uint32_t w[8] = {u0.x, u0.y, u0.z, u0.w, u1.x, u1.y, u1.z, u1.w};
+#pragma unroll
+    for (int i = 0; i < 8; ++i) {
+        const float2 f = unpack_bf16x2(w[i]);
+        v[2 * i] = f.x; v[2 * i + 1] = f.y;
+    }
+}
+
+__device__ __forceinline__ void tmem_st_f16(uint32_t taddr, const float* v) {
+    uint32_t u[16];
+#pragma unroll
+    for (int j = 0; j < 16; ++j) u[j] = __float_as_uint(v[j]);
+    tc::tmem_st16(taddr, u);
+}
+
+// Per-layer vectors staged in shared memory once per CTA:
+// [l * w] bias of layer l (l = 0: b_in), [(L+1) w] w_o, [(L+2) w] W_in[:, 0].
+struct ParamOffsets {
+    unsigned long long bin, Win, wo, bo, b[kFusedMaxDepth + 1];
+};
+
+__device__ __forceinline__ void stage_params(float* ptab, const float* th, const ParamOffsets& o, int L, int w,
+                                             int K0) {
+    const int n = (L + 3) * w;
+    for (int i = threadIdx.x; i < n; i += blockDim.x) {
+        const int l = i / w, c = i % w;
+        float v;
+        if (l <= L) v = th[(l == 0 ? o.bin : o.b[l]) + c];
+        else if (l == L + 1) v = th[o.wo + c];
+        else v = th[o.Win + (size_t)c * K0];
+        ptab[i] = v;
+    }
+}
+
+// ---------------------------------------------------------------- producer / MMA roles
+
+// Warp 0, one lane: stream the weight slices of every contraction of every
+// tile of this CTA through the ring.
+template <class Sched>
+__device__ void producer_role(const Sched& sch, int ntiles, int nstages, uint8_t* ring, uint64_t* bfull,
+                              uint64_t* bempty, volatile int* abort_flag, int* err) {
+    int it = 0;
+    bool ok = true;
+    for (int t = blockIdx.x; t < ntiles && ok; t += gridDim.x) {
+        for (int q = 0; q < sch.nq() && ok; ++q) {
+            const FGemm g = sch.gemm(q);
+            for (int kc = 0; kc < g.nk; ++kc, ++it) {
+                const int s = it % nstages;
+                const uint32_t ph = (uint32_t)(it / nstages) & 1u;
+                if (*abort_flag || !tc::mbar_wait(&bempty[s], ph ^ 1u, tc::kWaitBudget)) {
+                    ok = false;
+                    break;
+                }
+                tc::mbar_expect_tx(&bfull[s], (uint32_t)g.N * 128u);
+                tc::tma_load_2d(ring + s * kFStageBytes, g.map, &bfull[s], kc * 64, 0);
+            }
+        }
+    }
+    if (!ok) {
+        if (err) atomicExch(err, 2);
+        *abort_flag = 1;
+    }
+}
+
+// Warp 1, one lane: per contraction wait for the operand tile, then issue
+// K = 16 MMAs slice by slice, releasing each ring stage and finally
+// signalling the accumulator.
+template <class Sched>
+__device__ void mma_role(const Sched& sch, int ntiles, int nstages, uint32_t abase0, uint32_t abase1,
+                         uint32_t rbase, uint32_t tmem, uint64_t* bfull, uint64_t* bempty, uint64_t* accf,
+                         uint64_t* aready, volatile int* abort_flag, int* err) {
+    int it = 0, qg = 0;
+    bool ok = true;
+    for (int t = blockIdx.x; t < ntiles && ok; t += gridDim.x) {
+        for (int q = 0; q < sch.nq() && ok; ++q, ++qg) {
+            if (*abort_flag || !tc::mbar_wait(aready, (uint32_t)qg & 1u, tc::kWaitBudget)) {
+                ok = false;
+                break;
+            }
+            tc::tc_fence_after();
+            const FGemm g = sch.gemm(q);
+            const uint32_t abase = g.asel ? abase1 : abase0;
+            const uint32_t idesc = tc::idesc_bf16(128, g.N, 0, 0);
+            for (int kc = 0; kc < g.nk; ++kc, ++it) {
+                const int s = it % nstages;
+                const uint32_t ph = (uint32_t)(it / nstages) & 1u;
+                if (*abort_flag || !tc::mbar_wait(&bfull[s], ph, tc::kWaitBudget)) {
+                    ok = false;
+                    break;
+                }
+                tc::tc_fence_after();
+                const int nsteps = min(4, (g.K - kc * 64 + 15) / 16);
+                for (int k = 0; k < nsteps; ++k) {
+                    const uint64_t ad = tc::sdesc_sw128(abase + (uint32_t)kc * 16384u + 32u * k, 16u);
+                    const uint64_t bd = tc::sdesc_sw128(rbase + (uint32_t)s * kFStageBytes + 32u * k, 16u);
+                    tc::mma_bf16(tmem, ad, bd, idesc, (kc > 0 || k > 0) ? 1u : 0u);
+                }
+                tc::mma_commit(&bempty[s]);
+            }
+            if (ok) tc::mma_commit(accf);
+        }
+    }
+    if (!ok) {
+        if (err) atomicExch(err, 2);
+        *abort_flag = 1;
+    }
+}
+
+// Epilogue threads: hand contraction q's operand over to the MMA issuer.
+__device__ __forceinline__ void epi_handoff(uint64_t* aready) {
+    tc::tmem_wait_st();
+    tc::fence_async_shared();
+    tc::tc_fence_before();
+    tc::mbar_arrive(aready);
+}
+
+// Load a [128 x ncols] FP32 row block (row p of X, zero beyond P or ncols) into
+// a BF16 tile, and optionally copy it to a BF16 global row of width ldo.
+__device__ __forceinline__ void load_input_tile(uint8_t* tile, const float* src, int p, bool valid, int ncols,
+                                                int ncols_pad, int row, int eg, bf16* gcopy, int ldo) {
+    for (int u = eg; u < ncols_pad / 8; u += 2) {
+        const int c = u * 8;
+        float v[8];
+#pragma unroll
+        for (int j = 0; j < 8; ++j) v[j] = (valid && c + j < ncols) ? __ldg(src + (size_t)p * ncols + c + j) : 0.f;
+        st_tile8(tile, row, c, v);
+        if (gcopy && valid) {
+            uint4 u4;
+            u4.x = pack_bf16x2(v[0], v[1]); u4.y = pack_bf16x2(v[2], v[3]);
+            u4.z = pack_bf16x2(v[4], v[5]); u4.w = pack_bf16x2(v[6], v[7]);
+            *reinterpret_cast<uint4*>(gcopy + (size_t)p * ldo + c) = u4;
+        }
+    }
+}
+
+// ---------------------------------------------------------------- forward + Z
+
+struct FwdZArgs {
+    CUtensorMap wf[kFusedMaxDepth + 1];  // forward weights: [0] W_in[:,1:] (box {64, w}), [l] W_l
+    CUtensorMap wr[kFusedMaxDepth + 1];  // reverse weights: [0] W_in[:,1:]^T (box {64, Dn}), [l] W_l^T
+    const float* X;                      // [P x D]
+    const float* theta;
+    float* Y;                            // [P], zeroed before the launch
+    float* Z;                            // [P x D]
+    bf16* G;                             // g_l = G + l * G_stride, rows of wp
+    unsigned long long G_stride;
+    bf16* scratch;                       // per CTA: L x 128 x w (act'(a_l), l < L)
+    ParamOffsets off;
+    int P, M, D, Dp, Dn, w, wp, L, ntiles;
+    float dt;
+    int* err;
+};
+
+struct FwdZSched {
+    const FwdZArgs* a;
+    __device__ int nq() const { return 2 * a->L + 2; }
+    // 0: lift, 1..L: layers, L+1..2L: reverse through layer 2L+1-q, 2L+1: Z
+    __device__ FGemm gemm(int q) const {
+        FGemm g;
+        const int L = a->L;
+        g.asel = 0;
+        if (q == 0) { g.map = &a->wf[0]; g.nk = a->Dp / 64; g.K = a->D; g.N = a->w; }
+        else if (q <= L) { g.map = &a->wf[q]; g.nk = a->wp / 64; g.K = a->w; g.N = a->w; }
+        else if (q <= 2 * L) { g.map = &a->wr[2 * L + 1 - q]; g.nk = a->wp / 64; g.K = a->w; g.N = a->w; }
+        else { g.map = &a->wr[0]; g.nk = a->wp / 64; g.K = a->w; g.N = a->Dn; }
+        return g;
+    }
+};
+
+template <int ACT, bool RES>
+__global__ void __launch_bounds__(kFThreads, 1) k_fused_fwdz(const __grid_constant__ FwdZArgs a) {
+    extern __shared__ uint8_t smem_raw[];
+    uint8_t* smem = (uint8_t*)(((uintptr_t)smem_raw + 1023) & ~(uintptr_t)1023);
+    uint8_t* tile = smem;
+    uint8_t* ring = smem + kFTileBytes;
+    float* ptab = (float*)(ring + kFwdStages * kFStageBytes);
+    uint64_t* bfull = (uint64_t*)(ptab + (a.L + 3) * a.w);
+    uint64_t* bempty = bfull + kFwdStages;
+    uint64_t* accf = bempty + kFwdStages;
+    uint64_t* aready = accf + 1;
+    uint32_t* tslot = (uint32_t*)(aready + 1);
+    volatile int* abort_flag = (volatile int*)(tslot + 1);
+
+    const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+    const int L = a.L;
+    const FwdZSched sch{&a};
+
+    stage_params(ptab, a.theta, a.off, L, a.w, a.D + 1);
+    if (threadIdx.x == 0) {
+        for (int s = 0; s < kFwdStages; ++s) {
+            tc::mbar_init(&bfull[s], 1);
+            tc::mbar_init(&bempty[s], 1);
+        }
+        tc::mbar_init(accf, 1);
+        tc::mbar_init(aready, kFEpiThreads);
+        *abort_flag = 0;
+        tc::fence_mbar_init();
+    }
+    if (warp == 1) {
+        tc::tmem_alloc(tslot, 512);
+        tc::tmem_relinquish();
+    }
+    tc::tc_fence_before();
+    __syncthreads();
+    tc::tc_fence_after();
+    const uint32_t tmem = *tslot;
+
+    if (warp == 0) {
+        if (lane == 0) producer_role(sch, a.ntiles, kFwdStages, ring, bfull, bempty, abort_flag, a.err);
+    } else if (warp == 1) {
+        if (lane == 0)
+            mma_role(sch, a.ntiles, kFwdStages, tc::smem_u32(tile), tc::smem_u32(tile), tc::smem_u32(ring), tmem,
+                     bfull, bempty, accf, aready, abort_flag, a.err);
+    } else {
+        const int eg = (warp - 2) >> 2;
+        const int lg = warp & 3;
+        const int row = lg * 32 + lane;
+        const uint32_t tacc = tmem + ((uint32_t)(lg * 32) << 16);
+        const uint32_t tres = tacc + 256u;
+        const float* wo = ptab + (L + 1) * a.w;
+        const float* win0 = ptab + (L + 2) * a.w;
+        const int nq = sch.nq();
+        int qg = 0;
+        bool ok = true;
+        for (int t = blockIdx.x; t < a.ntiles && ok; t += gridDim.x) {
+            const int p = t * 128 + row;
+            const bool valid = p < a.P;
+            const float tval = valid ? (float)(p / a.M) * a.dt : 0.f;
+            load_input_tile(tile, a.X, p, valid, a.D, a.Dp, row, eg, nullptr, 0);
+            epi_handoff(aready);
+            for (int q = 0; q < nq; ++q, ++qg) {
+                if (!tc::mbar_wait(accf, (uint32_t)qg & 1u, tc::kWaitBudget)) {
+                    ok = false;
+                    break;
+                }
+                tc::tc_fence_after();
+                if (q <= L) {
+                    // forward layer l: a = acc + b_l (+ t W_in[:,0]); h_l = [h_{l-1}] + act(a)
+                    const int l = q;
+                    const float* bias = ptab + l * a.w;
+                    bf16* scr = a.scratch + ((size_t)blockIdx.x * L + l) * 128 * a.w + (size_t)row * a.w;
+                    float ypart = 0.f;
+                    for (int ch = eg; ch < a.w / 16; ch += 2) {
+                        const int c0 = ch * 16;
+                        uint32_t rv[16], rr[16];
+                        tc::tmem_ld16(tacc + (uint32_t)c0, rv);
+                        if (RES && l >= 1) tc::tmem_ld16(tres + (uint32_t)c0, rr);
+                        tc::tmem_wait_ld();
+                        float h[16], d1[16];
+#pragma unroll
+                        for (int j = 0; j < 16; ++j) {
+                            float av = __uint_as_float(rv[j]) + bias[c0 + j];
+                            if (l == 0) av = fmaf(tval, win0[c0 + j], av);
+                            const Act3 f = act3_sfu<ACT>(av);
+                            h[j] = ((RES && l >= 1) ? __uint_as_float(rr[j]) : 0.f) + f.f;
+                            d1[j] = f.d1;
+                        }
+                        if (l < L) {
+                            st_tile8(tile, row, c0, h);
+                            st_tile8(tile, row, c0 + 8, h + 8);
+                            st_bf16x16(scr + c0, d1);
+                            if (RES) tmem_st_f16(tres + (uint32_t)c0, h);
+                        } else {
+                            // top: y = w_o^T h_L + b_o and e_L = act'(a_L) w_o
+                            float e[16];
+#pragma unroll
+                            for (int j = 0; j < 16; ++j) {
+                                ypart = fmaf(h[j], wo[c0 + j], ypart);
+                                e[j] = d1[j] * wo[c0 + j];
+                            }
+                            st_tile8(tile, row, c0, e);
+                            st_tile8(tile, row, c0 + 8, e + 8);
+                        }
+                    }
+                    // the two groups' partial sums commute exactly: deterministic
+                    if (l == L && valid) atomicAdd(a.Y + p, ypart + (eg == 0 ? __ldg(a.theta + a.off.bo) : 0.f));
+                } else if (q <= 2 * L) {
+                    // reverse through layer l: g_{l-1} = [g_l] + W_l^T e_l, e_{l-1} = act'(a_{l-1}) g_{l-1}
+                    const int l = 2 * L + 1 - q;
+                    const bf16* scr = a.scratch + ((size_t)blockIdx.x * L + (l - 1)) * 128 * a.w + (size_t)row * a.w;
+                    bf16* gout = a.G + (size_t)(l - 1) * a.G_stride + (size_t)p * a.wp;
+                    for (int ch = eg; ch < a.w / 16; ch += 2) {
+                        const int c0 = ch * 16;
+                        float d1[16];
+                        ld_bf16x16(scr + c0, d1);
+                        uint32_t rv[16], rr[16];
+                        tc::tmem_ld16(tacc + (uint32_t)c0, rv);
+                        if (RES && l < L) tc::tmem_ld16(tres + (uint32_t)c0, rr);
+                        tc::tmem_wait_ld();
+                        float g[16], e[16];
+#pragma unroll
+                        for (int j = 0; j < 16; ++j) {
+                            const float gl = RES ? (l == L ? wo[c0 + j] : __uint_as_float(rr[j])) : 0.f;
+                            g[j] = gl + __uint_as_float(rv[j]);
+                            e[j] = d1[j] * g[j];
+                        }
+                        if (valid) st_bf16x16(gout + c0, g);
+                        st_tile8(tile, row, c0, e);
+                        st_tile8(tile, row, c0 + 8, e + 8);
+                        if (RES) tmem_st_f16(tres + (uint32_t)c0, g);
+                    }
+                } else {
+                    // Z = W_in[:,1:]^T e_0
+                    for (int ch = eg; ch < a.Dn / 16; ch += 2) {
+                        const int c0 = ch * 16;
+                        uint32_t rv[16];
+                        tc::tmem_ld16(tacc + (uint32_t)c0, rv);
+                        tc::tmem_wait_ld();
+                        if (valid) {
+#pragma unroll
+                            for (int j = 0; j < 16; ++j)
+                                if (c0 + j < a.D) a.Z[(size_t)p * a.D + c0 + j] = __uint_as_float(rv[j]);
+                        }
+                    }
+                }
+                if (q < nq - 1) epi_handoff(aready);
+            }
+        }
+        if (!ok) {
+            if (a.err) atomicExch(a.err, 2);
+            *abort_flag = 1;
+        }
+    }
+
+    tc::tc_fence_before();
+    __syncthreads();
+    if (warp == 1) {
+        tc::tc_fence_after();
+        tc::tmem_dealloc(tmem, 512);
+    }
+}
+
+// ---------------------------------------------------------------- tangent + adjoint
+
+struct BwdArgs {
+    CUtensorMap wf[kFusedMaxDepth + 1];
+    CUtensorMap wr[kFusedMaxDepth + 1];
+    const float* X;
+    const float* V;      // d loss / d Z_n  [P x D]
+    const float* alpha;  // d loss / d Y_n  [P]
+    const float* theta;
+    const bf16* G;       // g_l, l < L (from k_fused_fwdz)
+    unsigned long long G_stride;
+    bf16* Xb;            // BF16 copies of X and V, rows of Dp (weight-gradient operands)
+    bf16* Vb;
+    bf16* Hb;            // h_l, l = 0..L   rows of wp, layer stride OP_stride
+    bf16* HDb;           // h'_l
+    bf16* Eb;            // e_l = act'(a_l) g_l
+    bf16* ABb;           // abar_l
+    unsigned long long OP_stride;
+    bf16* scratch;       // per CTA: act'' (1 layer), act' (L+1 layers), S (L layers), each 128 x w
+    ParamOffsets off;
+    int P, M, D, Dp, w, wp, L, ntiles;
+    float dt;
+    int* err;
+};
+
+struct BwdSched {
+    const BwdArgs* a;
+    __device__ int nq() const { return 3 * a->L + 2; }
+    // 2l: forward layer l, 2l+1: tangent layer l (l = 0..L), 2L+2+j: adjoint through layer L-j
+    __device__ FGemm gemm(int q) const {
+        FGemm g;
+        const int L = a->L;
+        if (q < 2 * L + 2) {
+            const int l = q >> 1;
+            g.asel = q & 1;
+            g.map = &a->wf[l];
+            g.nk = (l == 0 ? a->Dp : a->wp) / 64;
+            g.K = l == 0 ? a->D : a->w;
+            g.N = a->w;
+        } else {
+            const int l = L - (q - (2 * L + 2));
+            g.asel = 0;
+            g.map = &a->wr[l];
+            g.nk = a->wp / 64;
+            g.K = a->w;
+            g.N = a->w;
+        }
+        return g;
+    }
+};
+
+template <int ACT, bool RES>
+__global__ void __launch_bounds__(kFThreads, 1) k_fused_bwd(const __grid_constant__ BwdArgs a) {
+    extern __shared__ uint8_t smem_raw[];
+    uint8_t* smem = (uint8_t*)(((uintptr_t)smem_raw + 1023) & ~(uintptr_t)1023);
+    uint8_t* tile_h = smem;                  // h_l during the forward, abar_l during the adjoint
+    uint8_t* tile_d = smem + kFTileBytes;    // h'_l
+    uint8_t* ring = smem + 2 * kFTileBytes;
+    float* ptab = (float*)(ring + kBwdStages * kFStageBytes);
+    uint64_t* bfull = (uint64_t*)(ptab + (a.L + 3) * a.w);
+    uint64_t* bempty = bfull + kBwdStages;
+    uint64_t* accf = bempty + kBwdStages;
+    uint64_t* aready = accf + 1;
+    uint32_t* tslot = (uint32_t*)(aready + 1);
+    volatile int* abort_flag = (volatile int*)(tslot + 1);
+
+    const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+    const int L = a.L;
+    const BwdSched sch{&a};
+
+    stage_params(ptab, a.theta, a.off, L, a.w, a.D + 1);
+    if (threadIdx.x == 0) {
+        for (int s = 0; s < kBwdStages; ++s) {
+            tc::mbar_init(&bfull[s], 1);
+            tc::mbar_init(&bempty[s], 1);
+        }
+        tc::mbar_init(accf, 1);
+        tc::mbar_init(aready, kFEpiThreads);
+        *abort_flag = 0;
+        tc::fence_mbar_init();
+    }
+    if (warp == 1) {
+        tc::tmem_alloc(tslot, 512);
+        tc::tmem_relinquish();
+    }
+    tc::tc_fence_before();
+    __syncthreads();
+    tc::tc_fence_after();
+    const uint32_t tmem = *tslot;
+
+    if (warp == 0) {
+        if (lane == 0) producer_role(sch, a.ntiles, kBwdStages, ring, bfull, bempty, abort_flag, a.err);
+    } else if (warp == 1) {
+        if (lane == 0)
+            mma_role(sch, a.ntiles, kBwdStages, tc::smem_u32(tile_h), tc::smem_u32(tile_d), tc::smem_u32(ring),
+                     tmem, bfull, bempty, accf, aready, abort_flag, a.err);
+    } else {
+        const int eg = (warp - 2) >> 2;
+        const int lg = warp & 3;
+        const int row = lg * 32 + lane;
+        const uint32_t tacc = tmem + ((uint32_t)(lg * 32) << 16);
+        const uint32_t tres = tacc + 256u;
+        const float* wo = ptab + (L + 1) * a.w;
+        const float* win0 = ptab + (L + 2) * a.w;
+        const size_t lay = (size_t)128 * a.w;
+        bf16* scr_base = a.scratch + (size_t)blockIdx.x * (2 * L + 2) * lay + (size_t)row * a.w;
+        bf16* scr_d2 = scr_base;                      // act''(a_l) of the current layer
+        bf16* scr_d1 = scr_base + lay;                // act'(a_l), l = 0..L
+        bf16* scr_S = scr_base + (size_t)(L + 2) * lay;  // S_l, l = 0..L-1
+        const int nq = sch.nq();
+        int qg = 0;
+        bool ok = true;
+        for (int t = blockIdx.x; t < a.ntiles && ok; t += gridDim.x) {
+            const int p = t * 128 + row;
+            const bool valid = p < a.P;
+            const float tval = valid ? (float)(p / a.M) * a.dt : 0.f;
+            const float alpha_p = valid ? __ldg(a.alpha + p) : 0.f;
+            // inputs: (t, X) for the forward, (0, v) for the tangent, and their BF16 copies
+            load_input_tile(tile_h, a.X, p, valid, a.D, a.Dp, row, eg, a.Xb, a.Dp);
+            load_input_tile(tile_d, a.V, p, valid, a.D, a.Dp, row, eg, a.Vb, a.Dp);
+            epi_handoff(aready);
+            for (int q = 0; q < nq; ++q, ++qg) {
+                if (!tc::mbar_wait(accf, (uint32_t)qg & 1u, tc::kWaitBudget)) {
+                    ok = false;
+                    break;
+                }
+                tc::tc_fence_after();
+                if (q < 2 * L + 2 && !(q & 1)) {
+                    // forward layer l (recomputed): h_l, act'(a_l), act''(a_l)
+                    const int l = q >> 1;
+                    const float* bias = ptab + l * a.w;
+                    bf16* hout = a.Hb + (size_t)l * a.OP_stride + (size_t)p * a.wp;
+                    for (int ch = eg; ch < a.w / 16; ch += 2) {
+                        const int c0 = ch * 16;
+                        uint32_t rv[16], rr[16];
+                        tc::tmem_ld16(tacc + (uint32_t)c0, rv);
+                        if (RES && l >= 1) tc::tmem_ld16(tres + (uint32_t)c0, rr);
+                        tc::tmem_wait_ld();
+                        float h[16], d1[16], d2[16];
+#pragma unroll
+                        for (int j = 0; j < 16; ++j) {
+                            float av = __uint_as_float(rv[j]) + bias[c0 + j];
+                            if (l == 0) av = fmaf(tval, win0[c0 + j], av);
+                            const Act3 f = act3_sfu<ACT>(av);
+                            h[j] = ((RES && l >= 1) ? __uint_as_float(rr[j]) : 0.f) + f.f;
+                            d1[j] = f.d1;
+                            d2[j] = f.d2;
+                        }
+                        st_tile8(tile_h, row, c0, h);
+                        st_tile8(tile_h, row, c0 + 8, h + 8);
+                        if (valid) st_bf16x16(hout + c0, h);
+                        st_bf16x16(scr_d1 + (size_t)l * lay + c0, d1);
+                        st_bf16x16(scr_d2 + c0, d2);
+                        if (RES) tmem_st_f16(tres + (uint32_t)c0, h);
+                    }
+                } else if (q < 2 * L + 2) {
+                    // tangent layer l: h'_l = [h'_{l-1}] + act'(a_l) a'_l, S_l = act''(a_l) a'_l g_l,
+                    // e_l = act'(a_l) g_l; at the top also abar_L and hbar_L = alpha w_o
+                    const int l = q >> 1;
+                    const bf16* gin = a.G + (size_t)l * a.G_stride + (size_t)p * a.wp;
+                    bf16* hdout = a.HDb + (size_t)l * a.OP_stride + (size_t)p * a.wp;
+                    bf16* eout = a.Eb + (size_t)l * a.OP_stride + (size_t)p * a.wp;
+                    bf16* about = a.ABb + (size_t)L * a.OP_stride + (size_t)p * a.wp;
+                    for (int ch = eg; ch < a.w / 16; ch += 2) {
+                        const int c0 = ch * 16;
+                        float d1[16], d2[16], g[16], hp[16];
+                        ld_bf16x16(scr_d1 + (size_t)l * lay + c0, d1);
+                        ld_bf16x16(scr_d2 + c0, d2);
+                        if (l < L && valid) ld_bf16x16(gin + c0, g);
+                        else {
+#pragma unroll
+                            for (int j = 0; j < 16; ++j) g[j] = l == L ? wo[c0 + j] : 0.f;
+                        }
+                        if (RES && l >= 1) {
+                            ld_tile8(tile_d, row, c0, hp);
+                            ld_tile8(tile_d, row, c0 + 8, hp + 8);
+                        }
+                        uint32_t rv[16];
+                        tc::tmem_ld16(tacc + (uint32_t)c0, rv);
+                        tc::tmem_wait_ld();
+                        float hd[16], S[16], e[16];
+#pragma unroll
+                        for (int j = 0; j < 16; ++j) {
+                            const float ad = __uint_as_float(rv[j]);
+                            hd[j] = ((RES && l >= 1) ? hp[j] : 0.f) + d1[j] * ad;
+                            S[j] = d2[j] * ad * g[j];
+                            e[j] = d1[j] * g[j];
+                        }
+                        st_tile8(tile_d, row, c0, hd);
+                        st_tile8(tile_d, row, c0 + 8, hd + 8);
+                        if (valid) {
+                            st_bf16x16(hdout + c0, hd);
+                            st_bf16x16(eout + c0, e);
+                        }
+                        if (l < L) {
+                            st_bf16x16(scr_S + (size_t)l * lay + c0, S);
+                        } else {
+                            float ab[16], hb[16];
+#pragma unroll
+                            for (int j = 0; j < 16; ++j) {
+                                hb[j] = alpha_p * wo[c0 + j];
+                                ab[j] = d1[j] * hb[j] + S[j];
+                            }
+                            st_tile8(tile_h, row, c0, ab);
+                            st_tile8(tile_h, row, c0 + 8, ab + 8);
+                            if (valid) st_bf16x16(about + c0, ab);
+                            if (RES) tmem_st_f16(tres + (uint32_t)c0, hb);
+                        }
+                    }
+                } else {
+                    // adjoint through layer l: hbar_{l-1} = [hbar_l] + W_l^T abar_l,
+                    // abar_{l-1} = act'(a_{l-1}) hbar_{l-1} + S_{l-1}
+                    const int l = L - (q - (2 * L + 2));
+                    bf16* about = a.ABb + (size_t)(l - 1) * a.OP_stride + (size_t)p * a.wp;
+                    for (int ch = eg; ch < a.w / 16; ch += 2) {
+                        const int c0 = ch * 16;
+                        float d1[16], S[16];
+                        ld_bf16x16(scr_d1 + (size_t)(l - 1) * lay + c0, d1);
+                        ld_bf16x16(scr_S + (size_t)(l - 1) * lay + c0, S);
+                        uint32_t rv[16], rr[16];
+                        tc::tmem_ld16(tacc + (uint32_t)c0, rv);
+                        if (RES) tc::tmem_ld16(tres + (uint32_t)c0, rr);
+                        tc::tmem_wait_ld();
+                        float hb[16], ab[16];
+#pragma unroll
+                        for (int j = 0; j < 16; ++j) {
+                            hb[j] = (RES ? __uint_as_float(rr[j]) : 0.f) + __uint_as_float(rv[j]);
+                            ab[j] = d1[j] * hb[j] + S[j];
+                        }
+                        if (l > 1) {
+                            st_tile8(tile_h, row, c0, ab);
+                            st_tile8(tile_h, row, c0 + 8, ab + 8);
+                        }
+                        if (valid) st_bf16x16(about + c0, ab);
+                        if (RES) tmem_st_f16(tres + (uint32_t)c0, hb);
+                    }
+                }
+                if (q < nq - 1) epi_handoff(aready);
+            }
+        }
+        if (!ok) {
+            if (a.err) atomicExch(a.err, 2);
+            *abort_flag = 1;
+        }
+    }
+
+    tc::tc_fence_before();
+    __syncthreads();
+    if (warp == 1) {
+        tc::tc_fence_after();
+        tc::tmem_dealloc(tmem, 512);
+    }
+}
+
+// ---------------------------------------------------------------- host launchers
+
+static size_t fwdz_smem_bytes(int L, int w) {
+    return 1024 + kFTileBytes + (size_t)kFwdStages * kFStageBytes + (size_t)(L + 3) * w * 4 + 256;
+}
+static size_t bwd_smem_bytes(int L, int w) {
+    return 1024 + 2 * kFTileBytes + (size_t)kBwdStages * kFStageBytes + (size_t)(L + 3) * w * 4 + 256;
+}
+
+template <class K, class A>
+static cudaError_t launch_fused(K kernel, const A& args, int grid, size_t smem, cudaStream_t st) {
+    cudaError_t e = cudaFuncSetAttribute(kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+    if (e != cudaSuccess) return e;
+    kernel<<<grid, kFThreads, smem, st>>>(args);
+    return cudaGetLastError();
+}
+
+static ParamOffsets param_offsets(const fbsde_ctx* c) {
+    ParamOffsets o;
+    std::memset(&o, 0, sizeof(o));
+    o.bin = c->pl.bin; o.Win = c->pl.Win; o.wo = c->pl.wo; o.bo = c->pl.bo;
+    for (int l = 1; l <= c->L; ++l) o.b[l] = c->pl.b[l];
+    return o;
+}
+
+fbsde_status fused_forward(fbsde_ctx* c, const float* theta) {
+    Bf16Work* b = c->bf;
+    FwdZArgs a;
+    std::memset(&a, 0, sizeof(a));
+    a.wf[0] = b->mWinx;
+    a.wr[0] = b->mWinxT;
+    for (int l = 1; l <= c->L; ++l) {
+        a.wf[l] = b->mW[l];
+        a.wr[l] = b->mWT[l];
+    }
+    a.X = c->X; a.theta = theta; a.Y = c->Y; a.Z = c->Z;
+    a.G = b->G; a.G_stride = b->G_stride; a.scratch = b->scratch;
+    a.off = param_offsets(c);
+    a.P = (int)c->P(); a.M = c->M; a.D = c->D; a.Dp = b->Dp; a.Dn = b->Dn; a.w = c->w; a.wp = b->wp;
+    a.L = c->L; a.ntiles = (a.P + 127) / 128; a.dt = (float)(c->T / c->N); a.err = b->err;
+    const int grid = a.ntiles < b->grid ? a.ntiles : b->grid;
+    FBSDE_CK(c, cudaMemsetAsync(c->Y, 0, (size_t)a.P * sizeof(float), c->stream));
+    const size_t smem = fwdz_smem_bytes(c->L, c->w);
+    const bool res = c->akind == FBSDE_RESNET;
+    const int tok = prof_begin(c, PROF_POINTS);
+    cudaError_t e;
+    if (c->act == FBSDE_TANH)
+        e = res ? launch_fused(k_fused_fwdz<FBSDE_TANH, true>, a, grid, smem, c->stream)
+                : launch_fused(k_fused_fwdz<FBSDE_TANH, false>, a, grid, smem, c->stream);
+    else
+        e = res ? launch_fused(k_fused_fwdz<FBSDE_SIN, true>, a, grid, smem, c->stream)
+                : launch_fused(k_fused_fwdz<FBSDE_SIN, false>, a, grid, smem, c->stream);
+    // algorithmic flops: lift + L layers forward, L reverse layers and the Z contraction
+    const double P = a.P, w = a.w, D = a.D;
+    prof_end(c, PROF_POINTS, tok, 2.0 * P * w * (2.0 * D + 2.0 * c->L * w));
+    if (e != cudaSuccess) return set_err(c, FBSDE_ERR_CUDA, std::string("fused forward: ") + cudaGetErrorString(e));
+    ++c->n_launch;
+    return FBSDE_OK;
+}
+
+fbsde_status fused_backward(fbsde_ctx* c, const float* theta) {
+    Bf16Work* b = c->bf;
+    BwdArgs a;
+    std::memset(&a, 0, sizeof(a));
+    a.wf[0] = b->mWinx;
+    for (int l = 1; l <= c->L; ++l) {
+        a.wf[l] = b->mW[l];
+        a.wr[l] = b->mWT[l];
+    }
+    a.X = c->X; a.V = c->V; a.alpha = c->alpha; a.theta = theta;
+    a.G = b->G; a.G_stride = b->G_stride;
+    a.Xb = b->Xb; a.Vb = b->Vb;
+    a.Hb = b->Hb[0]; a.HDb = b->HDb[0]; a.Eb = b->Eb[0]; a.ABb = b->ABb[0];
+    a.OP_stride = b->OP_stride;
+    a.scratch = b->scratch;
+    a.off = param_offsets(c);
+    a.P = (int)c->P(); a.M = c->M; a.D = c->D; a.Dp = b->Dp; a.w = c->w; a.wp = b->wp;
+    a.L = c->L; a.ntiles = (a.P + 127) / 128; a.dt = (float)(c->T / c->N); a.err = b->err;
+    const int grid = a.ntiles < b->grid ? a.ntiles : b->grid;
+    const size_t smem = bwd_smem_bytes(c->L, c->w);
+    const bool res = c->akind == FBSDE_RESNET;
+    const int tok = prof_begin(c, PROF_POINTS);
+    cudaError_t e;
+    if (c->act == FBSDE_TANH)
+        e = res ? launch_fused(k_fused_bwd<FBSDE_TANH, true>, a, grid, smem, c->stream)
+                : launch_fused(k_fused_bwd<FBSDE_TANH, false>, a, grid, smem, c->stream);
+    else
+        e = res ? launch_fused(k_fused_bwd<FBSDE_SIN, true>, a, grid, smem, c->stream)
+                : launch_fused(k_fused_bwd<FBSDE_SIN, false>, a, grid, smem, c->stream);
+    // algorithmic flops: tangent (lift + L layers) and adjoint (L layers); the
+    // forward recomputation is overhead and not counted
+    const double P = a.P, w = a.w, D = a.D;
+    prof_end(c, PROF_POINTS, tok, 2.0 * P * w * (D + 2.0 * c->L * w));
+    if (e != cudaSuccess) return set_err(c, FBSDE_ERR_CUDA, std::string("fused backward: ") + cudaGetErrorString(e));
+    ++c->n_launch;
+    return FBSDE_OK;
+}
+
+}  // namespace fbsde

@@ -157,7 +157,7 @@ fbsde_status nais_project(fbsde_ctx* ctx, float* theta);
 fbsde_status bf16_create(fbsde_ctx* ctx);
 void bf16_destroy(fbsde_ctx* ctx);
 fbsde_status bf16_prepare_weights(fbsde_ctx* ctx, const float* theta);
-fbsde_status bf16_forward(fbsde_ctx* ctx, const float* theta);
+fbsde_status bf16_forward(fbsde_ctx* ctx, const float* theta, bool for_grad);
 fbsde_status bf16_backward(fbsde_ctx* ctx, const float* theta, float* grad);
 
 // Helpers of the FP32 form reused by the BF16 form.

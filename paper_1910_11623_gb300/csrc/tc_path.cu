@@ -14,10 +14,9 @@
 
 #include "internal.cuh"
 #include "tc_gemm.cuh"
+#include "bf16_work.cuh"
 
 namespace fbsde {
-
-typedef __nv_bfloat16 bf16;
 
 static inline size_t rup(size_t x, size_t m) { return (x + m - 1) / m * m; }
 static inline unsigned nblk(size_t n, int bs) { return (unsigned)((n + bs - 1) / bs); }
@@ -39,7 +38,7 @@ static PFN_cuTensorMapEncodeTiled_v12000 encode_fn() {
 
 // Row-major BF16 matrix [outer x inner] with row stride ld (elements), box
 // {64, box_outer}, 128-byte swizzle, zero fill outside the matrix.
-static bool map2d(CUtensorMap* m, const void* base, uint64_t inner, uint64_t outer, uint64_t ld,
+bool map2d(CUtensorMap* m, const void* base, uint64_t inner, uint64_t outer, uint64_t ld,
                   uint32_t box_outer) {
     auto fn = encode_fn();
     if (!fn) return false;
@@ -54,24 +53,6 @@ static bool map2d(CUtensorMap* m, const void* base, uint64_t inner, uint64_t out
 
 // ------------------------------------------------------------------ workspace
 
-struct Bf16Work {
-    int Dp, Dn, wp;  // D padded to 64 (operand rows), D padded to 16 (MMA N), w padded to 64
-    void* mem = nullptr;
-    bf16 *Xb, *Vb;
-    bf16 *Hb[kMaxDepth + 1], *Eb[kMaxDepth + 1], *HDb[kMaxDepth + 1], *ABb[kMaxDepth + 1];
-    float *Af[kMaxDepth + 1], *Hf[kMaxDepth + 1], *Gf[kMaxDepth + 1], *HDf[kMaxDepth + 1];
-    float *Sf[kMaxDepth + 1], *HBf[kMaxDepth + 1];
-    bf16 *Winx, *WinxT, *W[kMaxDepth + 1], *WT[kMaxDepth + 1], *Bx[kMaxDepth + 1], *BxT[kMaxDepth + 1];
-    float* colpart;
-    int* err;
-    // NT operand maps (box rows 128)
-    CUtensorMap mXb, mVb, mHb[kMaxDepth + 1], mEb[kMaxDepth + 1], mHDb[kMaxDepth + 1], mABb[kMaxDepth + 1];
-    // weight maps (box rows = N of the contraction)
-    CUtensorMap mWinx, mWinxT, mW[kMaxDepth + 1], mWT[kMaxDepth + 1], mBx[kMaxDepth + 1], mBxT[kMaxDepth + 1];
-    // MN-major maps for the weight gradients (box {64, 64})
-    CUtensorMap tX, tV, tH[kMaxDepth + 1], tE[kMaxDepth + 1], tHD[kMaxDepth + 1], tAB[kMaxDepth + 1];
-};
-
 constexpr int kColSplits = 128;
 
 fbsde_status bf16_create(fbsde_ctx* c) {
@@ -83,13 +64,26 @@ fbsde_status bf16_create(fbsde_ctx* c) {
     b->Dn = (int)rup(D, 16);
     b->wp = (int)rup(w, 64);
     const size_t Pm = c->Pmax();
+    b->OP_stride = rup(Pm * b->wp, 128);
+    const size_t nl = (size_t)L + 1;
+    // per-tile fused kernels: FC / ResNet, depth <= kFusedMaxDepth, D <= 256
+    b->fused = c->akind != FBSDE_NAIS && L <= kFusedMaxDepth && b->Dp <= 256;
+    if (b->fused) {
+        int dev = 0, sms = 0;
+        FBSDE_CK(c, cudaGetDevice(&dev));
+        FBSDE_CK(c, cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev));
+        b->grid = sms;
+        b->G_stride = b->OP_stride;
+    }
+    // the layered sweeps keep FP32 copies of every per-layer tensor; the fused
+    // kernels keep them on chip and need only the BF16 operands
+    const bool layered_f32 = !b->fused;
     size_t bytes = 0;
     auto add = [&](size_t n) { bytes += rup(n, 256); };
     add(2 * Pm * b->Dp * sizeof(bf16));
-    for (int l = 0; l <= L; ++l) {
-        for (int k = 0; k < 4; ++k) add(Pm * b->wp * sizeof(bf16));
-        for (int k = 0; k < 6; ++k) add(Pm * w * sizeof(float));
-    }
+    for (int k = 0; k < 4; ++k) add(nl * b->OP_stride * sizeof(bf16));
+    if (layered_f32)
+        for (int k = 0; k < 6; ++k) add(nl * Pm * w * sizeof(float));
     add((size_t)w * b->Dp * 2); add((size_t)b->Dn * b->wp * 2);
     for (int l = 1; l <= L; ++l) {
         add((size_t)w * b->wp * 2); add((size_t)w * b->wp * 2);
@@ -97,6 +91,10 @@ fbsde_status bf16_create(fbsde_ctx* c) {
     }
     add((size_t)kColSplits * (rup(w, 16) + 16) * sizeof(float));
     add(256);
+    if (b->fused) {
+        add((size_t)(L > 0 ? L : 1) * b->G_stride * sizeof(bf16));
+        add((size_t)b->grid * (2 * L + 2) * 128 * w * sizeof(bf16));
+    }
     cudaError_t e = cudaMalloc(&b->mem, bytes);
     if (e != cudaSuccess) {
         cudaGetLastError();
@@ -109,12 +107,19 @@ fbsde_status bf16_create(fbsde_ctx* c) {
     auto take = [&](size_t n) { char* p = cur; cur += rup(n, 256); return (void*)p; };
     b->Xb = (bf16*)take(Pm * b->Dp * sizeof(bf16));
     b->Vb = (bf16*)take(Pm * b->Dp * sizeof(bf16));
+    bf16* blk[4];
+    for (int k = 0; k < 4; ++k) blk[k] = (bf16*)take(nl * b->OP_stride * sizeof(bf16));
+    float* fblk[6] = {};
+    if (layered_f32)
+        for (int k = 0; k < 6; ++k) fblk[k] = (float*)take(nl * Pm * w * sizeof(float));
     for (int l = 0; l <= L; ++l) {
-        b->Hb[l] = (bf16*)take(Pm * b->wp * 2); b->Eb[l] = (bf16*)take(Pm * b->wp * 2);
-        b->HDb[l] = (bf16*)take(Pm * b->wp * 2); b->ABb[l] = (bf16*)take(Pm * b->wp * 2);
-        b->Af[l] = (float*)take(Pm * w * 4); b->Hf[l] = (float*)take(Pm * w * 4);
-        b->Gf[l] = (float*)take(Pm * w * 4); b->HDf[l] = (float*)take(Pm * w * 4);
-        b->Sf[l] = (float*)take(Pm * w * 4); b->HBf[l] = (float*)take(Pm * w * 4);
+        b->Hb[l] = blk[0] + l * b->OP_stride; b->Eb[l] = blk[1] + l * b->OP_stride;
+        b->HDb[l] = blk[2] + l * b->OP_stride; b->ABb[l] = blk[3] + l * b->OP_stride;
+        if (layered_f32) {
+            const size_t o = (size_t)l * Pm * w;
+            b->Af[l] = fblk[0] + o; b->Hf[l] = fblk[1] + o; b->Gf[l] = fblk[2] + o;
+            b->HDf[l] = fblk[3] + o; b->Sf[l] = fblk[4] + o; b->HBf[l] = fblk[5] + o;
+        }
     }
     b->Winx = (bf16*)take((size_t)w * b->Dp * 2);
     b->WinxT = (bf16*)take((size_t)b->Dn * b->wp * 2);
@@ -124,6 +129,10 @@ fbsde_status bf16_create(fbsde_ctx* c) {
     }
     b->colpart = (float*)take((size_t)kColSplits * (rup(w, 16) + 16) * sizeof(float));
     b->err = (int*)take(256);
+    if (b->fused) {
+        b->G = (bf16*)take((size_t)(L > 0 ? L : 1) * b->G_stride * sizeof(bf16));
+        b->scratch = (bf16*)take((size_t)b->grid * (2 * L + 2) * 128 * w * sizeof(bf16));
+    }
 
     bool ok = true;
     const uint64_t P64 = Pm;
@@ -161,24 +170,6 @@ void bf16_destroy(fbsde_ctx* c) {
 }
 
 // ------------------------------------------------------------------ activations
-
-// act and its first two derivatives with fast SFU math (BF16 form).  tanh
-// from e = exp(-2|a|): tanh = sign(a) (1 - e) / (1 + e), tanh' = 4 e / (1 + e)^2
-// (no cancellation where tanh saturates), tanh'' = -2 tanh tanh'.
-__device__ __forceinline__ Act3 act3_fast(int act, float a) {
-    Act3 r;
-    if (act == FBSDE_SIN) {
-        float s, c;
-        __sincosf(a, &s, &c);
-        r.f = s; r.d1 = c; r.d2 = -s;
-    } else {
-        const float e = __expf(-2.f * fabsf(a));
-        const float q = __fdividef(1.f, 1.f + e);
-        const float t = copysignf((1.f - e) * q, a);
-        r.f = t; r.d1 = 4.f * e * q * q; r.d2 = -2.f * t * r.d1;
-    }
-    return r;
-}
 
 __device__ __forceinline__ void ld16f(const float* p, float (&v)[16]) {
     const float4* q = reinterpret_cast<const float4*>(p);
@@ -485,8 +476,10 @@ fbsde_status bf16_prepare_weights(fbsde_ctx* c, const float* theta) {
 
 // ------------------------------------------------------------------ forward
 
-fbsde_status bf16_forward(fbsde_ctx* c, const float* theta) {
+fbsde_status bf16_forward(fbsde_ctx* c, const float* theta, bool for_grad) {
     Bf16Work* b = c->bf;
+    (void)for_grad;
+    if (b->fused) return fused_forward(c, theta);
     const int w = c->w, L = c->L, D = c->D, K0 = D + 1, act = c->act, wp = b->wp;
     const int P = (int)c->P();
     const ParamLayout& pl = c->pl;
@@ -545,6 +538,10 @@ fbsde_status bf16_forward(fbsde_ctx* c, const float* theta) {
 
 fbsde_status bf16_backward(fbsde_ctx* c, const float* theta, float* grad) {
     Bf16Work* b = c->bf;
+    if (b->fused) {
+        FBSDE_TRY(fused_backward(c, theta));
+        return bf16_wgrad_tail(c, theta, grad);
+    }
     const int w = c->w, L = c->L, D = c->D, K0 = D + 1, act = c->act, wp = b->wp;
     const int P = (int)c->P();
     const ParamLayout& pl = c->pl;
@@ -580,6 +577,18 @@ fbsde_status bf16_backward(fbsde_ctx* c, const float* theta, float* grad) {
         FBSDE_TRY(tc_launch<false>(c, PROF_POINTS, a, 1, e, 2.0 * P * w * (double)w));
     }
 
+    return bf16_wgrad_tail(c, theta, grad);
+}
+
+// Weight gradients from the BF16 operands the sweeps left in HBM: W_l, W_in
+// (and NAIS B_l) by tensor-core contractions over all points, biases and the
+// read-out by fixed-order column sums.
+fbsde_status bf16_wgrad_tail(fbsde_ctx* c, const float* theta, float* grad) {
+    Bf16Work* b = c->bf;
+    const int w = c->w, L = c->L, D = c->D, K0 = D + 1, wp = b->wp;
+    const int P = (int)c->P();
+    const ParamLayout& pl = c->pl;
+    const bool nais = c->akind == FBSDE_NAIS;
     // weight gradients: contractions over all points on the tensor cores
     for (int l = 1; l <= L; ++l) {
         TcArgs a = nt_args(c, w, w);
@@ -605,8 +614,13 @@ fbsde_status bf16_backward(fbsde_ctx* c, const float* theta, float* grad) {
         FBSDE_TRY(colsum(c, PROF_WGRAD, b->ABb[0], true, wp, w, 1, nullptr, grad + pl.Win, K0, 0));
     }
     // dw_o = sum_p alpha_p h_L(p) + h'_L(p);  db_o = sum_p alpha_p
-    FBSDE_TRY(colsum(c, PROF_WGRAD, b->Hf[L], false, w, w, 2, c->alpha, grad + pl.wo, 1, 0));
-    FBSDE_TRY(colsum(c, PROF_WGRAD, b->HDf[L], false, w, w, 0, nullptr, grad + pl.wo, 1, 1));
+    if (b->fused) {
+        FBSDE_TRY(colsum(c, PROF_WGRAD, b->Hb[L], true, wp, w, 2, c->alpha, grad + pl.wo, 1, 0));
+        FBSDE_TRY(colsum(c, PROF_WGRAD, b->HDb[L], true, wp, w, 0, nullptr, grad + pl.wo, 1, 1));
+    } else {
+        FBSDE_TRY(colsum(c, PROF_WGRAD, b->Hf[L], false, w, w, 2, c->alpha, grad + pl.wo, 1, 0));
+        FBSDE_TRY(colsum(c, PROF_WGRAD, b->HDf[L], false, w, w, 0, nullptr, grad + pl.wo, 1, 1));
+    }
     FBSDE_TRY(colsum(c, PROF_WGRAD, c->alpha, false, 1, 1, 0, nullptr, grad + pl.bo, 1, 0));
     return launch_check_finite(c, grad, pl.total);
 }
