@@ -49,6 +49,7 @@ constexpr int kBwdStages = 2;
 struct FGemm {
     const CUtensorMap* map;
     int nk, K, N, asel;  // K slices, contraction length, output columns, A tile (0 or 1)
+    int dual;            // 1: also multiply tile 1 by the same weights into TMEM columns 256..
 };
 
 // ---------------------------------------------------------------- small helpers
@@ -173,6 +174,7 @@ __device__ void mma_role(const Sched& sch, int ntiles, int nstages, uint32_t aba
             const FGemm g = sch.gemm(q);
             const uint32_t abase = g.asel ? abase1 : abase0;
             const uint32_t idesc = tc::idesc_bf16(128, g.N, 0, 0);
+            const bool dual = g.dual != 0;
             for (int kc = 0; kc < g.nk; ++kc, ++it) {
                 const int s = it % nstages;
                 const uint32_t ph = (uint32_t)(it / nstages) & 1u;
@@ -186,6 +188,10 @@ __device__ void mma_role(const Sched& sch, int ntiles, int nstages, uint32_t aba
                     const uint64_t ad = tc::sdesc_sw128(abase + (uint32_t)kc * 16384u + 32u * k, 16u);
                     const uint64_t bd = tc::sdesc_sw128(rbase + (uint32_t)s * kFStageBytes + 32u * k, 16u);
                     tc::mma_bf16(tmem, ad, bd, idesc, (kc > 0 || k > 0) ? 1u : 0u);
+                    if (dual) {
+                        const uint64_t ad1 = tc::sdesc_sw128(abase1 + (uint32_t)kc * 16384u + 32u * k, 16u);
+                        tc::mma_bf16(tmem + 256u, ad1, bd, idesc, (kc > 0 || k > 0) ? 1u : 0u);
+                    }
                 }
                 tc::mma_commit(&bempty[s]);
             }
@@ -251,6 +257,7 @@ struct FwdZSched {
         FGemm g;
         const int L = a->L;
         g.asel = 0;
+        g.dual = 0;
         if (q == 0) { g.map = &a->wf[0]; g.nk = a->Dp / 64; g.K = a->D; g.N = a->w; }
         else if (q <= L) { g.map = &a->wf[q]; g.nk = a->wp / 64; g.K = a->w; g.N = a->w; }
         else if (q <= 2 * L) { g.map = &a->wr[2 * L + 1 - q]; g.nk = a->wp / 64; g.K = a->w; g.N = a->w; }
@@ -449,21 +456,23 @@ struct BwdArgs {
 
 struct BwdSched {
     const BwdArgs* a;
-    __device__ int nq() const { return 3 * a->L + 2; }
-    // 2l: forward layer l, 2l+1: tangent layer l (l = 0..L), 2L+2+j: adjoint through layer L-j
+    __device__ int nq() const { return 2 * a->L + 1; }
+    // l = q (0..L): forward and tangent contractions of layer l together (two
+    // accumulators, one weight stream); q = L+1+j: adjoint through layer L-j
     __device__ FGemm gemm(int q) const {
         FGemm g;
         const int L = a->L;
-        if (q < 2 * L + 2) {
-            const int l = q >> 1;
-            g.asel = q & 1;
-            g.map = &a->wf[l];
-            g.nk = (l == 0 ? a->Dp : a->wp) / 64;
-            g.K = l == 0 ? a->D : a->w;
+        if (q <= L) {
+            g.asel = 0;
+            g.dual = 1;
+            g.map = &a->wf[q];
+            g.nk = (q == 0 ? a->Dp : a->wp) / 64;
+            g.K = q == 0 ? a->D : a->w;
             g.N = a->w;
         } else {
-            const int l = L - (q - (2 * L + 2));
+            const int l = L - (q - (L + 1));
             g.asel = 0;
+            g.dual = 0;
             g.map = &a->wr[l];
             g.nk = a->wp / 64;
             g.K = a->w;
@@ -473,11 +482,14 @@ struct BwdSched {
     }
 };
 
+// The backward recomputes the forward with the BF16 skip path of the tile (the
+// FP32 residual of k_fused_fwdz has no room here: TMEM holds both the forward
+// and the tangent accumulators), and carries the tangent h' in BF16 as well.
 template <int ACT, bool RES>
 __global__ void __launch_bounds__(kFThreads, 1) k_fused_bwd(const __grid_constant__ BwdArgs a) {
     extern __shared__ uint8_t smem_raw[];
     uint8_t* smem = (uint8_t*)(((uintptr_t)smem_raw + 1023) & ~(uintptr_t)1023);
-    uint8_t* tile_h = smem;                  // h_l during the forward, abar_l during the adjoint
+    uint8_t* tile_h = smem;                  // h_l in the up-sweep, abar_l in the down-sweep
     uint8_t* tile_d = smem + kFTileBytes;    // h'_l
     uint8_t* ring = smem + 2 * kFTileBytes;
     float* ptab = (float*)(ring + kBwdStages * kFStageBytes);
@@ -523,15 +535,14 @@ __global__ void __launch_bounds__(kFThreads, 1) k_fused_bwd(const __grid_constan
         const int lg = warp & 3;
         const int row = lg * 32 + lane;
         const uint32_t tacc = tmem + ((uint32_t)(lg * 32) << 16);
-        const uint32_t tres = tacc + 256u;
+        const uint32_t tsec = tacc + 256u;  // tangent accumulator in the up-sweep, hbar in the down-sweep
         const float* wo = ptab + (L + 1) * a.w;
         const float* win0 = ptab + (L + 2) * a.w;
         const size_t lay = (size_t)128 * a.w;
-        bf16* scr_base = a.scratch + (size_t)blockIdx.x * (2 * L + 2) * lay + (size_t)row * a.w;
-        bf16* scr_d2 = scr_base;                      // act''(a_l) of the current layer
-        bf16* scr_d1 = scr_base + lay;                // act'(a_l), l = 0..L
-        bf16* scr_S = scr_base + (size_t)(L + 2) * lay;  // S_l, l = 0..L-1
+        bf16* scr_d1 = a.scratch + (size_t)blockIdx.x * (2 * L + 2) * lay + (size_t)row * a.w;  // act'(a_l), l < L
+        bf16* scr_S = scr_d1 + (size_t)L * lay;                                                 // S_l, l < L
         const int nq = sch.nq();
+        const int nch = a.w / 16;
         int qg = 0;
         bool ok = true;
         for (int t = blockIdx.x; t < a.ntiles && ok; t += gridDim.x) {
@@ -549,74 +560,78 @@ __global__ void __launch_bounds__(kFThreads, 1) k_fused_bwd(const __grid_constan
                     break;
                 }
                 tc::tc_fence_after();
-                if (q < 2 * L + 2 && !(q & 1)) {
-                    // forward layer l (recomputed): h_l, act'(a_l), act''(a_l)
-                    const int l = q >> 1;
+                if (q <= L) {
+                    // layer l forward and tangent:
+                    //   a = acc + b (+ t W_in[:,0]),  h_l = [h_{l-1}] + act(a)
+                    //   h'_l = [h'_{l-1}] + act'(a) a',  S_l = act''(a) a' g_l,  e_l = act'(a) g_l
+                    // at the top (l = L) also abar_L = act'(a_L) alpha w_o + S_L and hbar_L = alpha w_o
+                    const int l = q;
                     const float* bias = ptab + l * a.w;
-                    bf16* hout = a.Hb + (size_t)l * a.OP_stride + (size_t)p * a.wp;
-                    for (int ch = eg; ch < a.w / 16; ch += 2) {
-                        const int c0 = ch * 16;
-                        uint32_t rv[16], rr[16];
-                        tc::tmem_ld16(tacc + (uint32_t)c0, rv);
-                        if (RES && l >= 1) tc::tmem_ld16(tres + (uint32_t)c0, rr);
-                        tc::tmem_wait_ld();
-                        float h[16], d1[16], d2[16];
-#pragma unroll
-                        for (int j = 0; j < 16; ++j) {
-                            float av = __uint_as_float(rv[j]) + bias[c0 + j];
-                            if (l == 0) av = fmaf(tval, win0[c0 + j], av);
-                            const Act3 f = act3_sfu<ACT>(av);
-                            h[j] = ((RES && l >= 1) ? __uint_as_float(rr[j]) : 0.f) + f.f;
-                            d1[j] = f.d1;
-                            d2[j] = f.d2;
-                        }
-                        st_tile8(tile_h, row, c0, h);
-                        st_tile8(tile_h, row, c0 + 8, h + 8);
-                        if (valid) st_bf16x16(hout + c0, h);
-                        st_bf16x16(scr_d1 + (size_t)l * lay + c0, d1);
-                        st_bf16x16(scr_d2 + c0, d2);
-                        if (RES) tmem_st_f16(tres + (uint32_t)c0, h);
-                    }
-                } else if (q < 2 * L + 2) {
-                    // tangent layer l: h'_l = [h'_{l-1}] + act'(a_l) a'_l, S_l = act''(a_l) a'_l g_l,
-                    // e_l = act'(a_l) g_l; at the top also abar_L and hbar_L = alpha w_o
-                    const int l = q >> 1;
                     const bf16* gin = a.G + (size_t)l * a.G_stride + (size_t)p * a.wp;
+                    bf16* hout = a.Hb + (size_t)l * a.OP_stride + (size_t)p * a.wp;
                     bf16* hdout = a.HDb + (size_t)l * a.OP_stride + (size_t)p * a.wp;
                     bf16* eout = a.Eb + (size_t)l * a.OP_stride + (size_t)p * a.wp;
                     bf16* about = a.ABb + (size_t)L * a.OP_stride + (size_t)p * a.wp;
-                    for (int ch = eg; ch < a.w / 16; ch += 2) {
+                    const bool gmem = l < L && valid;
+                    uint4 gq0 = make_uint4(0, 0, 0, 0), gq1 = gq0;
+                    if (gmem && eg < nch) {
+                        gq0 = reinterpret_cast<const uint4*>(gin + eg * 16)[0];
+                        gq1 = reinterpret_cast<const uint4*>(gin + eg * 16)[1];
+                    }
+                    for (int ch = eg; ch < nch; ch += 2) {
                         const int c0 = ch * 16;
-                        float d1[16], d2[16], g[16], hp[16];
-                        ld_bf16x16(scr_d1 + (size_t)l * lay + c0, d1);
-                        ld_bf16x16(scr_d2 + c0, d2);
-                        if (l < L && valid) ld_bf16x16(gin + c0, g);
-                        else {
+                        // this chunk's g_l, then prefetch the next chunk's
+                        float g[16];
+                        if (l < L) {
+                            const uint32_t w8[8] = {gq0.x, gq0.y, gq0.z, gq0.w, gq1.x, gq1.y, gq1.z, gq1.w};
 #pragma unroll
-                            for (int j = 0; j < 16; ++j) g[j] = l == L ? wo[c0 + j] : 0.f;
+                            for (int i = 0; i < 8; ++i) {
+                                const float2 f2 = unpack_bf16x2(w8[i]);
+                                g[2 * i] = f2.x; g[2 * i + 1] = f2.y;
+                            }
+                            if (gmem && ch + 2 < nch) {
+                                gq0 = reinterpret_cast<const uint4*>(gin + c0 + 32)[0];
+                                gq1 = reinterpret_cast<const uint4*>(gin + c0 + 32)[1];
+                            }
+                        } else {
+#pragma unroll
+                            for (int j = 0; j < 16; ++j) g[j] = wo[c0 + j];
                         }
+                        uint32_t rf[16], rt[16];
+                        tc::tmem_ld16(tacc + (uint32_t)c0, rf);
+                        tc::tmem_ld16(tsec + (uint32_t)c0, rt);
+                        float hp[16], hdp[16];
                         if (RES && l >= 1) {
-                            ld_tile8(tile_d, row, c0, hp);
-                            ld_tile8(tile_d, row, c0 + 8, hp + 8);
+                            ld_tile8(tile_h, row, c0, hp);
+                            ld_tile8(tile_h, row, c0 + 8, hp + 8);
+                            ld_tile8(tile_d, row, c0, hdp);
+                            ld_tile8(tile_d, row, c0 + 8, hdp + 8);
                         }
-                        uint32_t rv[16];
-                        tc::tmem_ld16(tacc + (uint32_t)c0, rv);
                         tc::tmem_wait_ld();
-                        float hd[16], S[16], e[16];
+                        float h[16], hd[16], d1[16], S[16], e[16];
 #pragma unroll
                         for (int j = 0; j < 16; ++j) {
-                            const float ad = __uint_as_float(rv[j]);
-                            hd[j] = ((RES && l >= 1) ? hp[j] : 0.f) + d1[j] * ad;
-                            S[j] = d2[j] * ad * g[j];
-                            e[j] = d1[j] * g[j];
+                            float av = __uint_as_float(rf[j]) + bias[c0 + j];
+                            if (l == 0) av = fmaf(tval, win0[c0 + j], av);
+                            const Act3 f = act3_sfu<ACT>(av);
+                            const float ad = __uint_as_float(rt[j]);
+                            h[j] = ((RES && l >= 1) ? hp[j] : 0.f) + f.f;
+                            hd[j] = ((RES && l >= 1) ? hdp[j] : 0.f) + f.d1 * ad;
+                            S[j] = f.d2 * ad * g[j];
+                            e[j] = f.d1 * g[j];
+                            d1[j] = f.d1;
                         }
                         st_tile8(tile_d, row, c0, hd);
                         st_tile8(tile_d, row, c0 + 8, hd + 8);
                         if (valid) {
+                            st_bf16x16(hout + c0, h);
                             st_bf16x16(hdout + c0, hd);
                             st_bf16x16(eout + c0, e);
                         }
                         if (l < L) {
+                            st_tile8(tile_h, row, c0, h);
+                            st_tile8(tile_h, row, c0 + 8, h + 8);
+                            st_bf16x16(scr_d1 + (size_t)l * lay + c0, d1);
                             st_bf16x16(scr_S + (size_t)l * lay + c0, S);
                         } else {
                             float ab[16], hb[16];
@@ -628,22 +643,45 @@ __global__ void __launch_bounds__(kFThreads, 1) k_fused_bwd(const __grid_constan
                             st_tile8(tile_h, row, c0, ab);
                             st_tile8(tile_h, row, c0 + 8, ab + 8);
                             if (valid) st_bf16x16(about + c0, ab);
-                            if (RES) tmem_st_f16(tres + (uint32_t)c0, hb);
+                            if (RES) tmem_st_f16(tsec + (uint32_t)c0, hb);
                         }
                     }
                 } else {
                     // adjoint through layer l: hbar_{l-1} = [hbar_l] + W_l^T abar_l,
                     // abar_{l-1} = act'(a_{l-1}) hbar_{l-1} + S_{l-1}
-                    const int l = L - (q - (2 * L + 2));
+                    const int l = L - (q - (L + 1));
                     bf16* about = a.ABb + (size_t)(l - 1) * a.OP_stride + (size_t)p * a.wp;
-                    for (int ch = eg; ch < a.w / 16; ch += 2) {
+                    const bf16* d1src = scr_d1 + (size_t)(l - 1) * lay;
+                    const bf16* Ssrc = scr_S + (size_t)(l - 1) * lay;
+                    uint4 dq0 = make_uint4(0, 0, 0, 0), dq1 = dq0, sq0 = dq0, sq1 = dq0;
+                    if (eg < nch) {
+                        dq0 = reinterpret_cast<const uint4*>(d1src + eg * 16)[0];
+                        dq1 = reinterpret_cast<const uint4*>(d1src + eg * 16)[1];
+                        sq0 = reinterpret_cast<const uint4*>(Ssrc + eg * 16)[0];
+                        sq1 = reinterpret_cast<const uint4*>(Ssrc + eg * 16)[1];
+                    }
+                    for (int ch = eg; ch < nch; ch += 2) {
                         const int c0 = ch * 16;
                         float d1[16], S[16];
-                        ld_bf16x16(scr_d1 + (size_t)(l - 1) * lay + c0, d1);
-                        ld_bf16x16(scr_S + (size_t)(l - 1) * lay + c0, S);
+                        {
+                            const uint32_t a8[8] = {dq0.x, dq0.y, dq0.z, dq0.w, dq1.x, dq1.y, dq1.z, dq1.w};
+                            const uint32_t b8[8] = {sq0.x, sq0.y, sq0.z, sq0.w, sq1.x, sq1.y, sq1.z, sq1.w};
+#pragma unroll
+                            for (int i = 0; i < 8; ++i) {
+                                const float2 fa = unpack_bf16x2(a8[i]), fb = unpack_bf16x2(b8[i]);
+                                d1[2 * i] = fa.x; d1[2 * i + 1] = fa.y;
+                                S[2 * i] = fb.x; S[2 * i + 1] = fb.y;
+                            }
+                        }
+                        if (ch + 2 < nch) {
+                            dq0 = reinterpret_cast<const uint4*>(d1src + c0 + 32)[0];
+                            dq1 = reinterpret_cast<const uint4*>(d1src + c0 + 32)[1];
+                            sq0 = reinterpret_cast<const uint4*>(Ssrc + c0 + 32)[0];
+                            sq1 = reinterpret_cast<const uint4*>(Ssrc + c0 + 32)[1];
+                        }
                         uint32_t rv[16], rr[16];
                         tc::tmem_ld16(tacc + (uint32_t)c0, rv);
-                        if (RES) tc::tmem_ld16(tres + (uint32_t)c0, rr);
+                        if (RES) tc::tmem_ld16(tsec + (uint32_t)c0, rr);
                         tc::tmem_wait_ld();
                         float hb[16], ab[16];
 #pragma unroll
@@ -656,7 +694,7 @@ __global__ void __launch_bounds__(kFThreads, 1) k_fused_bwd(const __grid_constan
                             st_tile8(tile_h, row, c0 + 8, ab + 8);
                         }
                         if (valid) st_bf16x16(about + c0, ab);
-                        if (RES) tmem_st_f16(tres + (uint32_t)c0, hb);
+                        if (RES) tmem_st_f16(tsec + (uint32_t)c0, hb);
                     }
                 }
                 if (q < nq - 1) epi_handoff(aready);

@@ -53,7 +53,7 @@ bool map2d(CUtensorMap* m, const void* base, uint64_t inner, uint64_t outer, uin
 
 // ------------------------------------------------------------------ workspace
 
-constexpr int kColSplits = 128;
+constexpr int kColSplits = 296;
 
 fbsde_status bf16_create(fbsde_ctx* c) {
     Bf16Work* b = new (std::nothrow) Bf16Work();
@@ -343,20 +343,62 @@ __global__ void k_top_adj_b(size_t P, int w, int wp, const float* __restrict__ a
 
 // Partial column sums over a range of points, fixed order:
 // part[split][c] = sum_{p in split} wt(p) X[p][c], wt = 1 (mode 0), t_p (mode 1)
-// or wts[p] (mode 2).
+// or wts[p] (mode 2).  256 threads: 32 column lanes x 8 row lanes; a column
+// lane covers 8 consecutive columns with one 16- or 32-byte load per row (the
+// vector path needs ncols and ldx multiples of 8), the row lanes stride the
+// split's rows and are combined in shared memory in a fixed order.
 template <class T>
-__global__ void k_colsum(size_t P, int ncols, const T* __restrict__ X, int ldx, int mode,
-                         const float* __restrict__ wts, int M, float dt, float* __restrict__ part, size_t chunk) {
-    const int c = blockIdx.x * blockDim.x + threadIdx.x;
-    const int split = blockIdx.y;
-    if (c >= ncols) return;
+__global__ void __launch_bounds__(256) k_colsum(size_t P, int ncols, const T* __restrict__ X, int ldx, int mode,
+                                                const float* __restrict__ wts, int M, float dt,
+                                                float* __restrict__ part, size_t chunk) {
+    __shared__ float red[8][256 + 8];
+    const int tx = threadIdx.x & 31, ty = threadIdx.x >> 5;
+    const int split = blockIdx.x;
     const size_t p0 = (size_t)split * chunk, p1 = min(P, p0 + chunk);
-    float s = 0.f;
-    for (size_t p = p0; p < p1; ++p) {
-        const float wt = mode == 0 ? 1.f : mode == 1 ? (float)(p / M) * dt : wts[p];
-        s = fmaf(wt, (float)X[p * ldx + c], s);
+    const bool vec = (ncols % 8 == 0) && (ldx % 8 == 0);
+    for (int cb = 0; cb < ncols; cb += 256) {
+        float acc[8] = {0.f, 0.f, 0.f, 0.f, 0.f, 0.f, 0.f, 0.f};
+        const int c0 = cb + tx * 8;
+        for (size_t p = p0 + ty; p < p1; p += 8) {
+            const float wt = mode == 0 ? 1.f : mode == 1 ? (float)(p / M) * dt : wts[p];
+            const T* row = X + p * ldx;
+            if (vec) {
+                if (c0 < ncols) {
+                    float v[8];
+                    if (sizeof(T) == 2) {
+                        const uint4 u = *reinterpret_cast<const uint4*>(row + c0);
+                        const uint32_t w4[4] = {u.x, u.y, u.z, u.w};
+#pragma unroll
+                        for (int i = 0; i < 4; ++i) {
+                            const float2 f = __bfloat1622float2(*reinterpret_cast<const __nv_bfloat162*>(&w4[i]));
+                            v[2 * i] = f.x; v[2 * i + 1] = f.y;
+                        }
+                    } else {
+                        const float4 a = reinterpret_cast<const float4*>(row + c0)[0];
+                        const float4 b = reinterpret_cast<const float4*>(row + c0)[1];
+                        v[0] = a.x; v[1] = a.y; v[2] = a.z; v[3] = a.w; v[4] = b.x; v[5] = b.y; v[6] = b.z; v[7] = b.w;
+                    }
+#pragma unroll
+                    for (int i = 0; i < 8; ++i) acc[i] = fmaf(wt, v[i], acc[i]);
+                }
+            } else {
+#pragma unroll
+                for (int i = 0; i < 8; ++i)
+                    if (c0 + i < ncols) acc[i] = fmaf(wt, (float)row[c0 + i], acc[i]);
+            }
+        }
+#pragma unroll
+        for (int i = 0; i < 8; ++i) red[ty][tx * 8 + i] = acc[i];
+        __syncthreads();
+        const int c = cb + threadIdx.x;
+        if (threadIdx.x < 256 && c < ncols) {
+            float s = 0.f;
+#pragma unroll
+            for (int r = 0; r < 8; ++r) s += red[r][threadIdx.x];
+            part[(size_t)split * ncols + c] = s;
+        }
+        __syncthreads();
     }
-    part[(size_t)split * ncols + c] = s;
 }
 
 __global__ void k_colsum_reduce(const float* __restrict__ part, int splits, int ncols, float* __restrict__ out,
@@ -411,12 +453,11 @@ static fbsde_status colsum(fbsde_ctx* c, int cls, const void* X, bool is_bf16, i
     const size_t chunk = (P + kColSplits - 1) / kColSplits;
     const int splits = (int)((P + chunk - 1) / chunk);
     const float dt = (float)(c->T / c->N);
-    dim3 grid(nblk(ncols, 128), splits);
     const int tok = prof_begin(c, cls);
     if (is_bf16)
-        k_colsum<bf16><<<grid, 128, 0, c->stream>>>(P, ncols, (const bf16*)X, ldx, mode, wts, c->M, dt, b->colpart, chunk);
+        k_colsum<bf16><<<splits, 256, 0, c->stream>>>(P, ncols, (const bf16*)X, ldx, mode, wts, c->M, dt, b->colpart, chunk);
     else
-        k_colsum<float><<<grid, 128, 0, c->stream>>>(P, ncols, (const float*)X, ldx, mode, wts, c->M, dt, b->colpart, chunk);
+        k_colsum<float><<<splits, 256, 0, c->stream>>>(P, ncols, (const float*)X, ldx, mode, wts, c->M, dt, b->colpart, chunk);
     FBSDE_CK_LAUNCH(c);
     k_colsum_reduce<<<nblk(ncols, 128), 128, 0, c->stream>>>(b->colpart, splits, ncols, out, ldo, accumulate);
     prof_end(c, cls, tok, 2.0 * (double)P * ncols);
