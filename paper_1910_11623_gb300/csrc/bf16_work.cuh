@@ -71,15 +71,16 @@ struct Bf16Work {
     CUtensorMap tX, tV, tH[kMaxDepth + 1], tE[kMaxDepth + 1], tHD[kMaxDepth + 1], tAB[kMaxDepth + 1];
     // per-tile fused kernels (FC / ResNet, depth <= kFusedMaxDepth, D <= 256)
     bool fused = false;
+    CUtensorMap sHb, sHDb, sABb, sEb;  // layer stacks of the operands, box {64, 128, 1} (TMA stores)
     int grid = 0;          // persistent CTAs
     size_t OP_stride = 0;  // elements between consecutive layers of Hb, Eb, HDb, ABb
-    bf16* G = nullptr;     // g_l, l < L, [P x wp] each (written by the fused forward)
+    bf16* G = nullptr;     // g_l, l < L, per 128-row tile column-pair-major (written by the fused forward)
     size_t G_stride = 0;   // elements between consecutive g_l
     bf16* scratch = nullptr;  // per-CTA activation-derivative scratch
 };
 
 
-fbsde_status fused_forward(fbsde_ctx* c, const float* theta);
+fbsde_status fused_forward(fbsde_ctx* c, const float* theta, bool for_grad);
 fbsde_status fused_backward(fbsde_ctx* c, const float* theta);
 fbsde_status bf16_wgrad_tail(fbsde_ctx* c, const float* theta, float* grad);
 

@@ -106,6 +106,56 @@ __device__ __forceinline__ void tmem_st_f16(uint32_t taddr, const float* v) {
     tc::tmem_st16(taddr, u);
 }
 
+// Column-pair-major 128-row blocks (per-CTA scratch, g_l): the BF16 pair of
+// columns (2k, 2k+1) of row r is 32-bit word k * 128 + r, so the 32 rows of a
+// warp touch one 128-byte line per access instead of 32 lines.
+__device__ __forceinline__ void st_pm16(uint32_t* blk, int row, int c0, const float* v) {
+    uint32_t* q = blk + (c0 >> 1) * 128 + row;
+#pragma unroll
+    for (int k = 0; k < 8; ++k) q[k * 128] = pack_bf16x2(v[2 * k], v[2 * k + 1]);
+}
+__device__ __forceinline__ void ld_pm16_raw(const uint32_t* blk, int row, int c0, uint32_t (&u)[8]) {
+    const uint32_t* q = blk + (c0 >> 1) * 128 + row;
+#pragma unroll
+    for (int k = 0; k < 8; ++k) u[k] = q[k * 128];
+}
+__device__ __forceinline__ void unpack16(const uint32_t (&u)[8], float* v) {
+#pragma unroll
+    for (int k = 0; k < 8; ++k) {
+        const float2 f = unpack_bf16x2(u[k]);
+        v[2 * k] = f.x; v[2 * k + 1] = f.y;
+    }
+}
+
+// Tiles leave shared memory by TMA bulk stores issued by one epilogue thread.
+// Every phase that writes tiles is bracketed: before writing, the storing
+// thread waits until earlier stores have read their tiles and opens `tfree`;
+// after writing, every epilogue thread fences its writes for the async proxy
+// and arrives on `wdone`, which the storing thread waits for before it issues
+// the stores of this phase.  Both waits are bounded.
+struct StoreSync {
+    uint64_t* tfree;  // count 1: the storing thread
+    uint64_t* wdone;  // count 256: every epilogue thread
+    bool st_thread;
+    uint32_t phase;
+    __device__ bool before_write() {
+        if (st_thread) {
+            tc::tma_store_wait_read<0>();
+            tc::mbar_arrive(tfree);
+        }
+        return tc::mbar_wait(tfree, phase & 1u, tc::kWaitBudget);
+    }
+    // returns false on timeout; the storing thread may issue stores after it
+    __device__ bool after_write() {
+        tc::fence_async_shared();
+        tc::mbar_arrive(wdone);
+        bool ok = true;
+        if (st_thread) ok = tc::mbar_wait(wdone, phase & 1u, tc::kWaitBudget);
+        ++phase;
+        return ok;
+    }
+};
+
 // Per-layer vectors staged in shared memory once per CTA:
 // [l * w] bias of layer l (l = 0: b_in), [(L+1) w] w_o, [(L+2) w] W_in[:, 0].
 struct ParamOffsets {
@@ -236,13 +286,15 @@ __device__ __forceinline__ void load_input_tile(uint8_t* tile, const float* src,
 struct FwdZArgs {
     CUtensorMap wf[kFusedMaxDepth + 1];  // forward weights: [0] W_in[:,1:] (box {64, w}), [l] W_l
     CUtensorMap wr[kFusedMaxDepth + 1];  // reverse weights: [0] W_in[:,1:]^T (box {64, Dn}), [l] W_l^T
+    CUtensorMap eb;                      // e_l stack [L+1][P x wp] (TMA stores), when for_grad
     const float* X;                      // [P x D]
     const float* theta;
     float* Y;                            // [P], zeroed before the launch
     float* Z;                            // [P x D]
-    bf16* G;                             // g_l = G + l * G_stride, rows of wp
-    unsigned long long G_stride;
-    bf16* scratch;                       // per CTA: L x 128 x w (act'(a_l), l < L)
+    uint32_t* G;                         // g_l, l < L: word l * G_words + (tile * w/2 + k) * 128 + row
+    unsigned long long G_words;
+    uint32_t* scratch;                   // per CTA: L column-pair-major blocks (act'(a_l), l < L)
+    int for_grad;                        // also write g_l and e_l for the gradient
     ParamOffsets off;
     int P, M, D, Dp, Dn, w, wp, L, ntiles;
     float dt;
@@ -277,7 +329,9 @@ __global__ void __launch_bounds__(kFThreads, 1) k_fused_fwdz(const __grid_consta
     uint64_t* bempty = bfull + kFwdStages;
     uint64_t* accf = bempty + kFwdStages;
     uint64_t* aready = accf + 1;
-    uint32_t* tslot = (uint32_t*)(aready + 1);
+    uint64_t* tfree = aready + 1;
+    uint64_t* wdone = tfree + 1;
+    uint32_t* tslot = (uint32_t*)(wdone + 1);
     volatile int* abort_flag = (volatile int*)(tslot + 1);
 
     const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
@@ -292,6 +346,8 @@ __global__ void __launch_bounds__(kFThreads, 1) k_fused_fwdz(const __grid_consta
         }
         tc::mbar_init(accf, 1);
         tc::mbar_init(aready, kFEpiThreads);
+        tc::mbar_init(tfree, 1);
+        tc::mbar_init(wdone, kFEpiThreads);
         *abort_flag = 0;
         tc::fence_mbar_init();
     }
@@ -318,26 +374,37 @@ __global__ void __launch_bounds__(kFThreads, 1) k_fused_fwdz(const __grid_consta
         const uint32_t tres = tacc + 256u;
         const float* wo = ptab + (L + 1) * a.w;
         const float* win0 = ptab + (L + 2) * a.w;
+        const size_t blk = (size_t)(a.w / 2) * 128;  // words of one column-pair-major 128-row block
+        uint32_t* scr = a.scratch + (size_t)blockIdx.x * L * blk;
+        StoreSync ss{tfree, wdone, warp == 2 && lane == 0, 0u};
         const int nq = sch.nq();
+        const int nkw = a.wp / 64;
         int qg = 0;
         bool ok = true;
         for (int t = blockIdx.x; t < a.ntiles && ok; t += gridDim.x) {
             const int p = t * 128 + row;
             const bool valid = p < a.P;
             const float tval = valid ? (float)(p / a.M) * a.dt : 0.f;
+            uint32_t* gtile = a.G + (size_t)t * blk;
+            if (!ss.before_write()) { ok = false; break; }
             load_input_tile(tile, a.X, p, valid, a.D, a.Dp, row, eg, nullptr, 0);
-            epi_handoff(aready);
+            if (!ss.after_write()) { ok = false; break; }
+            tc::tc_fence_before();
+            tc::mbar_arrive(aready);
             for (int q = 0; q < nq; ++q, ++qg) {
                 if (!tc::mbar_wait(accf, (uint32_t)qg & 1u, tc::kWaitBudget)) {
                     ok = false;
                     break;
                 }
                 tc::tc_fence_after();
+                const bool writes_tile = q <= 2 * L;
+                if (writes_tile && !ss.before_write()) { ok = false; break; }
+                int store_layer = -1;  // e_l stored from the tile after this phase
                 if (q <= L) {
                     // forward layer l: a = acc + b_l (+ t W_in[:,0]); h_l = [h_{l-1}] + act(a)
                     const int l = q;
                     const float* bias = ptab + l * a.w;
-                    bf16* scr = a.scratch + ((size_t)blockIdx.x * L + l) * 128 * a.w + (size_t)row * a.w;
+                    uint32_t* sc = scr + (size_t)l * blk;
                     float ypart = 0.f;
                     for (int ch = eg; ch < a.w / 16; ch += 2) {
                         const int c0 = ch * 16;
@@ -357,7 +424,7 @@ __global__ void __launch_bounds__(kFThreads, 1) k_fused_fwdz(const __grid_consta
                         if (l < L) {
                             st_tile8(tile, row, c0, h);
                             st_tile8(tile, row, c0 + 8, h + 8);
-                            st_bf16x16(scr + c0, d1);
+                            st_pm16(sc, row, c0, d1);
                             if (RES) tmem_st_f16(tres + (uint32_t)c0, h);
                         } else {
                             // top: y = w_o^T h_L + b_o and e_L = act'(a_L) w_o
@@ -373,31 +440,34 @@ __global__ void __launch_bounds__(kFThreads, 1) k_fused_fwdz(const __grid_consta
                     }
                     // the two groups' partial sums commute exactly: deterministic
                     if (l == L && valid) atomicAdd(a.Y + p, ypart + (eg == 0 ? __ldg(a.theta + a.off.bo) : 0.f));
+                    if (l == L) store_layer = L;
                 } else if (q <= 2 * L) {
                     // reverse through layer l: g_{l-1} = [g_l] + W_l^T e_l, e_{l-1} = act'(a_{l-1}) g_{l-1}
                     const int l = 2 * L + 1 - q;
-                    const bf16* scr = a.scratch + ((size_t)blockIdx.x * L + (l - 1)) * 128 * a.w + (size_t)row * a.w;
-                    bf16* gout = a.G + (size_t)(l - 1) * a.G_stride + (size_t)p * a.wp;
+                    const uint32_t* sc = scr + (size_t)(l - 1) * blk;
+                    uint32_t* gout = gtile + (size_t)(l - 1) * a.G_words;
                     for (int ch = eg; ch < a.w / 16; ch += 2) {
                         const int c0 = ch * 16;
-                        float d1[16];
-                        ld_bf16x16(scr + c0, d1);
+                        uint32_t du[8];
+                        ld_pm16_raw(sc, row, c0, du);
                         uint32_t rv[16], rr[16];
                         tc::tmem_ld16(tacc + (uint32_t)c0, rv);
                         if (RES && l < L) tc::tmem_ld16(tres + (uint32_t)c0, rr);
                         tc::tmem_wait_ld();
-                        float g[16], e[16];
+                        float d1[16], g[16], e[16];
+                        unpack16(du, d1);
 #pragma unroll
                         for (int j = 0; j < 16; ++j) {
                             const float gl = RES ? (l == L ? wo[c0 + j] : __uint_as_float(rr[j])) : 0.f;
                             g[j] = gl + __uint_as_float(rv[j]);
                             e[j] = d1[j] * g[j];
                         }
-                        if (valid) st_bf16x16(gout + c0, g);
+                        if (a.for_grad) st_pm16(gout, row, c0, g);
                         st_tile8(tile, row, c0, e);
                         st_tile8(tile, row, c0 + 8, e + 8);
                         if (RES) tmem_st_f16(tres + (uint32_t)c0, g);
                     }
+                    store_layer = l - 1;
                 } else {
                     // Z = W_in[:,1:]^T e_0
                     for (int ch = eg; ch < a.Dn / 16; ch += 2) {
@@ -412,9 +482,21 @@ __global__ void __launch_bounds__(kFThreads, 1) k_fused_fwdz(const __grid_consta
                         }
                     }
                 }
-                if (q < nq - 1) epi_handoff(aready);
+                if (writes_tile) {
+                    if (!ss.after_write()) { ok = false; break; }
+                    if (ss.st_thread && a.for_grad && store_layer >= 0) {
+                        for (int k = 0; k < nkw; ++k) tc::tma_store_3d(&a.eb, tile + k * 16384, k * 64, t * 128, store_layer);
+                        tc::tma_store_commit();
+                    }
+                }
+                if (q < nq - 1) {
+                    tc::tmem_wait_st();
+                    tc::tc_fence_before();
+                    tc::mbar_arrive(aready);
+                }
             }
         }
+        if (ss.st_thread) tc::tma_store_wait_all<0>();
         if (!ok) {
             if (a.err) atomicExch(a.err, 2);
             *abort_flag = 1;
@@ -434,20 +516,16 @@ __global__ void __launch_bounds__(kFThreads, 1) k_fused_fwdz(const __grid_consta
 struct BwdArgs {
     CUtensorMap wf[kFusedMaxDepth + 1];
     CUtensorMap wr[kFusedMaxDepth + 1];
+    CUtensorMap hb, hdb, abb;  // operand stacks [L+1][P x wp] (TMA stores)
+    CUtensorMap xb, vb;        // BF16 copies of X and V, [P x Dp] (TMA stores)
     const float* X;
-    const float* V;      // d loss / d Z_n  [P x D]
-    const float* alpha;  // d loss / d Y_n  [P]
+    const float* V;            // d loss / d Z_n  [P x D]
+    const float* alpha;        // d loss / d Y_n  [P]
     const float* theta;
-    const bf16* G;       // g_l, l < L (from k_fused_fwdz)
-    unsigned long long G_stride;
-    bf16* Xb;            // BF16 copies of X and V, rows of Dp (weight-gradient operands)
-    bf16* Vb;
-    bf16* Hb;            // h_l, l = 0..L   rows of wp, layer stride OP_stride
-    bf16* HDb;           // h'_l
-    bf16* Eb;            // e_l = act'(a_l) g_l
-    bf16* ABb;           // abar_l
-    unsigned long long OP_stride;
-    bf16* scratch;       // per CTA: act'' (1 layer), act' (L+1 layers), S (L layers), each 128 x w
+    const uint32_t* G;         // g_l, l < L, column-pair-major per tile (from k_fused_fwdz)
+    unsigned long long G_words;
+    bf16* HbL;                 // h_L rows of wp (its tile slot holds abar_L)
+    uint32_t* scratch;         // per CTA: act'(a_l) and S_l, l < L, column-pair-major
     ParamOffsets off;
     int P, M, D, Dp, w, wp, L, ntiles;
     float dt;
@@ -497,7 +575,9 @@ __global__ void __launch_bounds__(kFThreads, 1) k_fused_bwd(const __grid_constan
     uint64_t* bempty = bfull + kBwdStages;
     uint64_t* accf = bempty + kBwdStages;
     uint64_t* aready = accf + 1;
-    uint32_t* tslot = (uint32_t*)(aready + 1);
+    uint64_t* tfree = aready + 1;
+    uint64_t* wdone = tfree + 1;
+    uint32_t* tslot = (uint32_t*)(wdone + 1);
     volatile int* abort_flag = (volatile int*)(tslot + 1);
 
     const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
@@ -512,6 +592,8 @@ __global__ void __launch_bounds__(kFThreads, 1) k_fused_bwd(const __grid_constan
         }
         tc::mbar_init(accf, 1);
         tc::mbar_init(aready, kFEpiThreads);
+        tc::mbar_init(tfree, 1);
+        tc::mbar_init(wdone, kFEpiThreads);
         *abort_flag = 0;
         tc::fence_mbar_init();
     }
@@ -538,11 +620,13 @@ __global__ void __launch_bounds__(kFThreads, 1) k_fused_bwd(const __grid_constan
         const uint32_t tsec = tacc + 256u;  // tangent accumulator in the up-sweep, hbar in the down-sweep
         const float* wo = ptab + (L + 1) * a.w;
         const float* win0 = ptab + (L + 2) * a.w;
-        const size_t lay = (size_t)128 * a.w;
-        bf16* scr_d1 = a.scratch + (size_t)blockIdx.x * (2 * L + 2) * lay + (size_t)row * a.w;  // act'(a_l), l < L
-        bf16* scr_S = scr_d1 + (size_t)L * lay;                                                 // S_l, l < L
+        const size_t blk = (size_t)(a.w / 2) * 128;
+        uint32_t* scr_d1 = a.scratch + (size_t)blockIdx.x * 2 * L * blk;  // act'(a_l), l < L
+        uint32_t* scr_S = scr_d1 + (size_t)L * blk;                       // S_l, l < L
+        StoreSync ss{tfree, wdone, warp == 2 && lane == 0, 0u};
         const int nq = sch.nq();
         const int nch = a.w / 16;
+        const int nkw = a.wp / 64, nkx = a.Dp / 64;
         int qg = 0;
         bool ok = true;
         for (int t = blockIdx.x; t < a.ntiles && ok; t += gridDim.x) {
@@ -550,49 +634,44 @@ __global__ void __launch_bounds__(kFThreads, 1) k_fused_bwd(const __grid_constan
             const bool valid = p < a.P;
             const float tval = valid ? (float)(p / a.M) * a.dt : 0.f;
             const float alpha_p = valid ? __ldg(a.alpha + p) : 0.f;
-            // inputs: (t, X) for the forward, (0, v) for the tangent, and their BF16 copies
-            load_input_tile(tile_h, a.X, p, valid, a.D, a.Dp, row, eg, a.Xb, a.Dp);
-            load_input_tile(tile_d, a.V, p, valid, a.D, a.Dp, row, eg, a.Vb, a.Dp);
-            epi_handoff(aready);
+            const uint32_t* gtile = a.G + (size_t)t * blk;
+            // inputs: (t, X) for the forward, (0, v) for the tangent
+            if (!ss.before_write()) { ok = false; break; }
+            load_input_tile(tile_h, a.X, p, valid, a.D, a.Dp, row, eg, nullptr, 0);
+            load_input_tile(tile_d, a.V, p, valid, a.D, a.Dp, row, eg, nullptr, 0);
+            if (!ss.after_write()) { ok = false; break; }
+            if (ss.st_thread) {
+                for (int k = 0; k < nkx; ++k) {
+                    tc::tma_store_2d(&a.xb, tile_h + k * 16384, k * 64, t * 128);
+                    tc::tma_store_2d(&a.vb, tile_d + k * 16384, k * 64, t * 128);
+                }
+                tc::tma_store_commit();
+            }
+            tc::tc_fence_before();
+            tc::mbar_arrive(aready);
             for (int q = 0; q < nq; ++q, ++qg) {
                 if (!tc::mbar_wait(accf, (uint32_t)qg & 1u, tc::kWaitBudget)) {
                     ok = false;
                     break;
                 }
                 tc::tc_fence_after();
+                if (!ss.before_write()) { ok = false; break; }
                 if (q <= L) {
                     // layer l forward and tangent:
                     //   a = acc + b (+ t W_in[:,0]),  h_l = [h_{l-1}] + act(a)
-                    //   h'_l = [h'_{l-1}] + act'(a) a',  S_l = act''(a) a' g_l,  e_l = act'(a) g_l
+                    //   h'_l = [h'_{l-1}] + act'(a) a',  S_l = act''(a) a' g_l
                     // at the top (l = L) also abar_L = act'(a_L) alpha w_o + S_L and hbar_L = alpha w_o
                     const int l = q;
                     const float* bias = ptab + l * a.w;
-                    const bf16* gin = a.G + (size_t)l * a.G_stride + (size_t)p * a.wp;
-                    bf16* hout = a.Hb + (size_t)l * a.OP_stride + (size_t)p * a.wp;
-                    bf16* hdout = a.HDb + (size_t)l * a.OP_stride + (size_t)p * a.wp;
-                    bf16* eout = a.Eb + (size_t)l * a.OP_stride + (size_t)p * a.wp;
-                    bf16* about = a.ABb + (size_t)L * a.OP_stride + (size_t)p * a.wp;
-                    const bool gmem = l < L && valid;
-                    uint4 gq0 = make_uint4(0, 0, 0, 0), gq1 = gq0;
-                    if (gmem && eg < nch) {
-                        gq0 = reinterpret_cast<const uint4*>(gin + eg * 16)[0];
-                        gq1 = reinterpret_cast<const uint4*>(gin + eg * 16)[1];
-                    }
+                    const uint32_t* gin = gtile + (size_t)l * a.G_words;
+                    uint32_t gq[8] = {0, 0, 0, 0, 0, 0, 0, 0};
+                    if (l < L && eg < nch) ld_pm16_raw(gin, row, eg * 16, gq);
                     for (int ch = eg; ch < nch; ch += 2) {
                         const int c0 = ch * 16;
-                        // this chunk's g_l, then prefetch the next chunk's
                         float g[16];
                         if (l < L) {
-                            const uint32_t w8[8] = {gq0.x, gq0.y, gq0.z, gq0.w, gq1.x, gq1.y, gq1.z, gq1.w};
-#pragma unroll
-                            for (int i = 0; i < 8; ++i) {
-                                const float2 f2 = unpack_bf16x2(w8[i]);
-                                g[2 * i] = f2.x; g[2 * i + 1] = f2.y;
-                            }
-                            if (gmem && ch + 2 < nch) {
-                                gq0 = reinterpret_cast<const uint4*>(gin + c0 + 32)[0];
-                                gq1 = reinterpret_cast<const uint4*>(gin + c0 + 32)[1];
-                            }
+                            unpack16(gq, g);
+                            if (ch + 2 < nch) ld_pm16_raw(gin, row, c0 + 32, gq);
                         } else {
 #pragma unroll
                             for (int j = 0; j < 16; ++j) g[j] = wo[c0 + j];
@@ -608,7 +687,7 @@ __global__ void __launch_bounds__(kFThreads, 1) k_fused_bwd(const __grid_constan
                             ld_tile8(tile_d, row, c0 + 8, hdp + 8);
                         }
                         tc::tmem_wait_ld();
-                        float h[16], hd[16], d1[16], S[16], e[16];
+                        float h[16], hd[16], d1[16], S[16];
 #pragma unroll
                         for (int j = 0; j < 16; ++j) {
                             float av = __uint_as_float(rf[j]) + bias[c0 + j];
@@ -618,22 +697,17 @@ __global__ void __launch_bounds__(kFThreads, 1) k_fused_bwd(const __grid_constan
                             h[j] = ((RES && l >= 1) ? hp[j] : 0.f) + f.f;
                             hd[j] = ((RES && l >= 1) ? hdp[j] : 0.f) + f.d1 * ad;
                             S[j] = f.d2 * ad * g[j];
-                            e[j] = f.d1 * g[j];
                             d1[j] = f.d1;
                         }
                         st_tile8(tile_d, row, c0, hd);
                         st_tile8(tile_d, row, c0 + 8, hd + 8);
-                        if (valid) {
-                            st_bf16x16(hout + c0, h);
-                            st_bf16x16(hdout + c0, hd);
-                            st_bf16x16(eout + c0, e);
-                        }
                         if (l < L) {
                             st_tile8(tile_h, row, c0, h);
                             st_tile8(tile_h, row, c0 + 8, h + 8);
-                            st_bf16x16(scr_d1 + (size_t)l * lay + c0, d1);
-                            st_bf16x16(scr_S + (size_t)l * lay + c0, S);
+                            st_pm16(scr_d1 + (size_t)l * blk, row, c0, d1);
+                            st_pm16(scr_S + (size_t)l * blk, row, c0, S);
                         } else {
+                            if (valid) st_bf16x16(a.HbL + (size_t)p * a.wp + c0, h);
                             float ab[16], hb[16];
 #pragma unroll
                             for (int j = 0; j < 16; ++j) {
@@ -642,42 +716,37 @@ __global__ void __launch_bounds__(kFThreads, 1) k_fused_bwd(const __grid_constan
                             }
                             st_tile8(tile_h, row, c0, ab);
                             st_tile8(tile_h, row, c0 + 8, ab + 8);
-                            if (valid) st_bf16x16(about + c0, ab);
                             if (RES) tmem_st_f16(tsec + (uint32_t)c0, hb);
                         }
+                    }
+                    if (!ss.after_write()) { ok = false; break; }
+                    if (ss.st_thread) {
+                        for (int k = 0; k < nkw; ++k) {
+                            tc::tma_store_3d(&a.hdb, tile_d + k * 16384, k * 64, t * 128, l);
+                            if (l < L) tc::tma_store_3d(&a.hb, tile_h + k * 16384, k * 64, t * 128, l);
+                            else tc::tma_store_3d(&a.abb, tile_h + k * 16384, k * 64, t * 128, L);
+                        }
+                        tc::tma_store_commit();
                     }
                 } else {
                     // adjoint through layer l: hbar_{l-1} = [hbar_l] + W_l^T abar_l,
                     // abar_{l-1} = act'(a_{l-1}) hbar_{l-1} + S_{l-1}
                     const int l = L - (q - (L + 1));
-                    bf16* about = a.ABb + (size_t)(l - 1) * a.OP_stride + (size_t)p * a.wp;
-                    const bf16* d1src = scr_d1 + (size_t)(l - 1) * lay;
-                    const bf16* Ssrc = scr_S + (size_t)(l - 1) * lay;
-                    uint4 dq0 = make_uint4(0, 0, 0, 0), dq1 = dq0, sq0 = dq0, sq1 = dq0;
+                    const uint32_t* d1src = scr_d1 + (size_t)(l - 1) * blk;
+                    const uint32_t* Ssrc = scr_S + (size_t)(l - 1) * blk;
+                    uint32_t dq[8] = {0, 0, 0, 0, 0, 0, 0, 0}, sq[8] = {0, 0, 0, 0, 0, 0, 0, 0};
                     if (eg < nch) {
-                        dq0 = reinterpret_cast<const uint4*>(d1src + eg * 16)[0];
-                        dq1 = reinterpret_cast<const uint4*>(d1src + eg * 16)[1];
-                        sq0 = reinterpret_cast<const uint4*>(Ssrc + eg * 16)[0];
-                        sq1 = reinterpret_cast<const uint4*>(Ssrc + eg * 16)[1];
+                        ld_pm16_raw(d1src, row, eg * 16, dq);
+                        ld_pm16_raw(Ssrc, row, eg * 16, sq);
                     }
                     for (int ch = eg; ch < nch; ch += 2) {
                         const int c0 = ch * 16;
                         float d1[16], S[16];
-                        {
-                            const uint32_t a8[8] = {dq0.x, dq0.y, dq0.z, dq0.w, dq1.x, dq1.y, dq1.z, dq1.w};
-                            const uint32_t b8[8] = {sq0.x, sq0.y, sq0.z, sq0.w, sq1.x, sq1.y, sq1.z, sq1.w};
-#pragma unroll
-                            for (int i = 0; i < 8; ++i) {
-                                const float2 fa = unpack_bf16x2(a8[i]), fb = unpack_bf16x2(b8[i]);
-                                d1[2 * i] = fa.x; d1[2 * i + 1] = fa.y;
-                                S[2 * i] = fb.x; S[2 * i + 1] = fb.y;
-                            }
-                        }
+                        unpack16(dq, d1);
+                        unpack16(sq, S);
                         if (ch + 2 < nch) {
-                            dq0 = reinterpret_cast<const uint4*>(d1src + c0 + 32)[0];
-                            dq1 = reinterpret_cast<const uint4*>(d1src + c0 + 32)[1];
-                            sq0 = reinterpret_cast<const uint4*>(Ssrc + c0 + 32)[0];
-                            sq1 = reinterpret_cast<const uint4*>(Ssrc + c0 + 32)[1];
+                            ld_pm16_raw(d1src, row, c0 + 32, dq);
+                            ld_pm16_raw(Ssrc, row, c0 + 32, sq);
                         }
                         uint32_t rv[16], rr[16];
                         tc::tmem_ld16(tacc + (uint32_t)c0, rv);
@@ -689,17 +758,24 @@ __global__ void __launch_bounds__(kFThreads, 1) k_fused_bwd(const __grid_constan
                             hb[j] = (RES ? __uint_as_float(rr[j]) : 0.f) + __uint_as_float(rv[j]);
                             ab[j] = d1[j] * hb[j] + S[j];
                         }
-                        if (l > 1) {
-                            st_tile8(tile_h, row, c0, ab);
-                            st_tile8(tile_h, row, c0 + 8, ab + 8);
-                        }
-                        if (valid) st_bf16x16(about + c0, ab);
+                        st_tile8(tile_h, row, c0, ab);
+                        st_tile8(tile_h, row, c0 + 8, ab + 8);
                         if (RES) tmem_st_f16(tsec + (uint32_t)c0, hb);
                     }
+                    if (!ss.after_write()) { ok = false; break; }
+                    if (ss.st_thread) {
+                        for (int k = 0; k < nkw; ++k) tc::tma_store_3d(&a.abb, tile_h + k * 16384, k * 64, t * 128, l - 1);
+                        tc::tma_store_commit();
+                    }
                 }
-                if (q < nq - 1) epi_handoff(aready);
+                if (q < nq - 1) {
+                    tc::tmem_wait_st();
+                    tc::tc_fence_before();
+                    tc::mbar_arrive(aready);
+                }
             }
         }
+        if (ss.st_thread) tc::tma_store_wait_all<0>();
         if (!ok) {
             if (a.err) atomicExch(a.err, 2);
             *abort_flag = 1;
@@ -717,10 +793,10 @@ __global__ void __launch_bounds__(kFThreads, 1) k_fused_bwd(const __grid_constan
 // ---------------------------------------------------------------- host launchers
 
 static size_t fwdz_smem_bytes(int L, int w) {
-    return 1024 + kFTileBytes + (size_t)kFwdStages * kFStageBytes + (size_t)(L + 3) * w * 4 + 256;
+    return 1024 + kFTileBytes + (size_t)kFwdStages * kFStageBytes + (size_t)(L + 3) * w * 4 + 512;
 }
 static size_t bwd_smem_bytes(int L, int w) {
-    return 1024 + 2 * kFTileBytes + (size_t)kBwdStages * kFStageBytes + (size_t)(L + 3) * w * 4 + 256;
+    return 1024 + 2 * kFTileBytes + (size_t)kBwdStages * kFStageBytes + (size_t)(L + 3) * w * 4 + 512;
 }
 
 template <class K, class A>
@@ -739,7 +815,7 @@ static ParamOffsets param_offsets(const fbsde_ctx* c) {
     return o;
 }
 
-fbsde_status fused_forward(fbsde_ctx* c, const float* theta) {
+fbsde_status fused_forward(fbsde_ctx* c, const float* theta, bool for_grad) {
     Bf16Work* b = c->bf;
     FwdZArgs a;
     std::memset(&a, 0, sizeof(a));
@@ -749,8 +825,10 @@ fbsde_status fused_forward(fbsde_ctx* c, const float* theta) {
         a.wf[l] = b->mW[l];
         a.wr[l] = b->mWT[l];
     }
+    a.eb = b->sEb;
     a.X = c->X; a.theta = theta; a.Y = c->Y; a.Z = c->Z;
-    a.G = b->G; a.G_stride = b->G_stride; a.scratch = b->scratch;
+    a.G = (uint32_t*)b->G; a.G_words = b->G_stride / 2; a.scratch = (uint32_t*)b->scratch;
+    a.for_grad = for_grad ? 1 : 0;
     a.off = param_offsets(c);
     a.P = (int)c->P(); a.M = c->M; a.D = c->D; a.Dp = b->Dp; a.Dn = b->Dn; a.w = c->w; a.wp = b->wp;
     a.L = c->L; a.ntiles = (a.P + 127) / 128; a.dt = (float)(c->T / c->N); a.err = b->err;
@@ -783,12 +861,11 @@ fbsde_status fused_backward(fbsde_ctx* c, const float* theta) {
         a.wf[l] = b->mW[l];
         a.wr[l] = b->mWT[l];
     }
+    a.hb = b->sHb; a.hdb = b->sHDb; a.abb = b->sABb; a.xb = b->mXb; a.vb = b->mVb;
     a.X = c->X; a.V = c->V; a.alpha = c->alpha; a.theta = theta;
-    a.G = b->G; a.G_stride = b->G_stride;
-    a.Xb = b->Xb; a.Vb = b->Vb;
-    a.Hb = b->Hb[0]; a.HDb = b->HDb[0]; a.Eb = b->Eb[0]; a.ABb = b->ABb[0];
-    a.OP_stride = b->OP_stride;
-    a.scratch = b->scratch;
+    a.G = (const uint32_t*)b->G; a.G_words = b->G_stride / 2;
+    a.HbL = b->Hb[c->L];
+    a.scratch = (uint32_t*)b->scratch;
     a.off = param_offsets(c);
     a.P = (int)c->P(); a.M = c->M; a.D = c->D; a.Dp = b->Dp; a.w = c->w; a.wp = b->wp;
     a.L = c->L; a.ntiles = (a.P + 127) / 128; a.dt = (float)(c->T / c->N); a.err = b->err;

@@ -51,6 +51,21 @@ bool map2d(CUtensorMap* m, const void* base, uint64_t inner, uint64_t outer, uin
               CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE) == CUDA_SUCCESS;
 }
 
+// Stack of `depth` row-major BF16 matrices [outer x inner] (row stride ld,
+// matrix stride mstride elements), box {64, box_outer, 1}, 128-byte swizzle.
+bool map3d(CUtensorMap* m, const void* base, uint64_t inner, uint64_t outer, uint64_t depth, uint64_t ld,
+           uint64_t mstride, uint32_t box_outer) {
+    auto fn = encode_fn();
+    if (!fn) return false;
+    cuuint64_t dims[3] = {inner, outer, depth};
+    cuuint64_t strides[2] = {ld * sizeof(bf16), mstride * sizeof(bf16)};
+    cuuint32_t box[3] = {64, box_outer, 1};
+    cuuint32_t es[3] = {1, 1, 1};
+    return fn(m, CU_TENSOR_MAP_DATA_TYPE_BFLOAT16, 3, const_cast<void*>(base), dims, strides, box, es,
+              CU_TENSOR_MAP_INTERLEAVE_NONE, CU_TENSOR_MAP_SWIZZLE_128B, CU_TENSOR_MAP_L2_PROMOTION_L2_256B,
+              CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE) == CUDA_SUCCESS;
+}
+
 // ------------------------------------------------------------------ workspace
 
 constexpr int kColSplits = 296;
@@ -73,7 +88,7 @@ fbsde_status bf16_create(fbsde_ctx* c) {
         FBSDE_CK(c, cudaGetDevice(&dev));
         FBSDE_CK(c, cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev));
         b->grid = sms;
-        b->G_stride = b->OP_stride;
+        b->G_stride = rup((Pm + 127) / 128 * 128 * (size_t)w, 128);
     }
     // the layered sweeps keep FP32 copies of every per-layer tensor; the fused
     // kernels keep them on chip and need only the BF16 operands
@@ -157,6 +172,12 @@ fbsde_status bf16_create(fbsde_ctx* c) {
         ok &= map2d(&b->mWT[l], b->WT[l], b->wp, w, b->wp, w);
         ok &= map2d(&b->mBx[l], b->Bx[l], b->Dp, w, b->Dp, w);
         ok &= map2d(&b->mBxT[l], b->BxT[l], b->wp, b->Dn, b->wp, b->Dn);
+    }
+    if (b->fused) {
+        ok &= map3d(&b->sHb, b->Hb[0], b->wp, P64, (uint64_t)L + 1, b->wp, b->OP_stride, 128);
+        ok &= map3d(&b->sHDb, b->HDb[0], b->wp, P64, (uint64_t)L + 1, b->wp, b->OP_stride, 128);
+        ok &= map3d(&b->sABb, b->ABb[0], b->wp, P64, (uint64_t)L + 1, b->wp, b->OP_stride, 128);
+        ok &= map3d(&b->sEb, b->Eb[0], b->wp, P64, (uint64_t)L + 1, b->wp, b->OP_stride, 128);
     }
     if (!ok) return set_err(c, FBSDE_ERR_CUDA, "cuTensorMapEncodeTiled failed (driver entry point or arguments)");
     return FBSDE_OK;
@@ -519,8 +540,7 @@ fbsde_status bf16_prepare_weights(fbsde_ctx* c, const float* theta) {
 
 fbsde_status bf16_forward(fbsde_ctx* c, const float* theta, bool for_grad) {
     Bf16Work* b = c->bf;
-    (void)for_grad;
-    if (b->fused) return fused_forward(c, theta);
+    if (b->fused) return fused_forward(c, theta, for_grad);
     const int w = c->w, L = c->L, D = c->D, K0 = D + 1, act = c->act, wp = b->wp;
     const int P = (int)c->P();
     const ParamLayout& pl = c->pl;
