@@ -287,6 +287,7 @@ struct FwdZArgs {
     CUtensorMap wf[kFusedMaxDepth + 1];  // forward weights: [0] W_in[:,1:] (box {64, w}), [l] W_l
     CUtensorMap wr[kFusedMaxDepth + 1];  // reverse weights: [0] W_in[:,1:]^T (box {64, Dn}), [l] W_l^T
     CUtensorMap eb;                      // e_l stack [L+1][P x wp] (TMA stores), when for_grad
+    CUtensorMap xin;                     // BF16 copy of X, [P x Dp], box {64, 128} (TMA loads)
     const float* X;                      // [P x D]
     const float* theta;
     float* Y;                            // [P], zeroed before the launch
@@ -331,7 +332,8 @@ __global__ void __launch_bounds__(kFThreads, 1) k_fused_fwdz(const __grid_consta
     uint64_t* aready = accf + 1;
     uint64_t* tfree = aready + 1;
     uint64_t* wdone = tfree + 1;
-    uint32_t* tslot = (uint32_t*)(wdone + 1);
+    uint64_t* xfull = wdone + 1;
+    uint32_t* tslot = (uint32_t*)(xfull + 1);
     volatile int* abort_flag = (volatile int*)(tslot + 1);
 
     const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
@@ -348,6 +350,7 @@ __global__ void __launch_bounds__(kFThreads, 1) k_fused_fwdz(const __grid_consta
         tc::mbar_init(aready, kFEpiThreads);
         tc::mbar_init(tfree, 1);
         tc::mbar_init(wdone, kFEpiThreads);
+        tc::mbar_init(xfull, 1);
         *abort_flag = 0;
         tc::fence_mbar_init();
     }
@@ -379,15 +382,21 @@ __global__ void __launch_bounds__(kFThreads, 1) k_fused_fwdz(const __grid_consta
         StoreSync ss{tfree, wdone, warp == 2 && lane == 0, 0u};
         const int nq = sch.nq();
         const int nkw = a.wp / 64;
-        int qg = 0;
+        int qg = 0, tcount = 0;
         bool ok = true;
         for (int t = blockIdx.x; t < a.ntiles && ok; t += gridDim.x) {
             const int p = t * 128 + row;
             const bool valid = p < a.P;
             const float tval = valid ? (float)(p / a.M) * a.dt : 0.f;
             uint32_t* gtile = a.G + (size_t)t * blk;
+            // network input (t enters as a per-row bias): the BF16 X rows by TMA
             if (!ss.before_write()) { ok = false; break; }
-            load_input_tile(tile, a.X, p, valid, a.D, a.Dp, row, eg, nullptr, 0);
+            if (ss.st_thread) {
+                tc::mbar_expect_tx(xfull, (uint32_t)(a.Dp / 64) * 16384u);
+                for (int k = 0; k < a.Dp / 64; ++k) tc::tma_load_2d(tile + k * 16384, &a.xin, xfull, k * 64, t * 128);
+            }
+            if (!tc::mbar_wait(xfull, (uint32_t)tcount & 1u, tc::kWaitBudget)) { ok = false; break; }
+            ++tcount;
             if (!ss.after_write()) { ok = false; break; }
             tc::tc_fence_before();
             tc::mbar_arrive(aready);
@@ -517,7 +526,7 @@ struct BwdArgs {
     CUtensorMap wf[kFusedMaxDepth + 1];
     CUtensorMap wr[kFusedMaxDepth + 1];
     CUtensorMap hb, hdb, abb;  // operand stacks [L+1][P x wp] (TMA stores)
-    CUtensorMap xb, vb;        // BF16 copies of X and V, [P x Dp] (TMA stores)
+    CUtensorMap xb, vb;        // BF16 copies of X and V, [P x Dp], box {64, 128} (TMA loads)
     const float* X;
     const float* V;            // d loss / d Z_n  [P x D]
     const float* alpha;        // d loss / d Y_n  [P]
@@ -577,7 +586,8 @@ __global__ void __launch_bounds__(kFThreads, 1) k_fused_bwd(const __grid_constan
     uint64_t* aready = accf + 1;
     uint64_t* tfree = aready + 1;
     uint64_t* wdone = tfree + 1;
-    uint32_t* tslot = (uint32_t*)(wdone + 1);
+    uint64_t* xfull = wdone + 1;
+    uint32_t* tslot = (uint32_t*)(xfull + 1);
     volatile int* abort_flag = (volatile int*)(tslot + 1);
 
     const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
@@ -594,6 +604,7 @@ __global__ void __launch_bounds__(kFThreads, 1) k_fused_bwd(const __grid_constan
         tc::mbar_init(aready, kFEpiThreads);
         tc::mbar_init(tfree, 1);
         tc::mbar_init(wdone, kFEpiThreads);
+        tc::mbar_init(xfull, 1);
         *abort_flag = 0;
         tc::fence_mbar_init();
     }
@@ -627,7 +638,7 @@ __global__ void __launch_bounds__(kFThreads, 1) k_fused_bwd(const __grid_constan
         const int nq = sch.nq();
         const int nch = a.w / 16;
         const int nkw = a.wp / 64, nkx = a.Dp / 64;
-        int qg = 0;
+        int qg = 0, tcount = 0;
         bool ok = true;
         for (int t = blockIdx.x; t < a.ntiles && ok; t += gridDim.x) {
             const int p = t * 128 + row;
@@ -635,18 +646,18 @@ __global__ void __launch_bounds__(kFThreads, 1) k_fused_bwd(const __grid_constan
             const float tval = valid ? (float)(p / a.M) * a.dt : 0.f;
             const float alpha_p = valid ? __ldg(a.alpha + p) : 0.f;
             const uint32_t* gtile = a.G + (size_t)t * blk;
-            // inputs: (t, X) for the forward, (0, v) for the tangent
+            // inputs: (t, X) for the forward, (0, v) for the tangent, BF16 rows by TMA
             if (!ss.before_write()) { ok = false; break; }
-            load_input_tile(tile_h, a.X, p, valid, a.D, a.Dp, row, eg, nullptr, 0);
-            load_input_tile(tile_d, a.V, p, valid, a.D, a.Dp, row, eg, nullptr, 0);
-            if (!ss.after_write()) { ok = false; break; }
             if (ss.st_thread) {
+                tc::mbar_expect_tx(xfull, (uint32_t)nkx * 2u * 16384u);
                 for (int k = 0; k < nkx; ++k) {
-                    tc::tma_store_2d(&a.xb, tile_h + k * 16384, k * 64, t * 128);
-                    tc::tma_store_2d(&a.vb, tile_d + k * 16384, k * 64, t * 128);
+                    tc::tma_load_2d(tile_h + k * 16384, &a.xb, xfull, k * 64, t * 128);
+                    tc::tma_load_2d(tile_d + k * 16384, &a.vb, xfull, k * 64, t * 128);
                 }
-                tc::tma_store_commit();
             }
+            if (!tc::mbar_wait(xfull, (uint32_t)tcount & 1u, tc::kWaitBudget)) { ok = false; break; }
+            ++tcount;
+            if (!ss.after_write()) { ok = false; break; }
             tc::tc_fence_before();
             tc::mbar_arrive(aready);
             for (int q = 0; q < nq; ++q, ++qg) {
@@ -826,6 +837,7 @@ fbsde_status fused_forward(fbsde_ctx* c, const float* theta, bool for_grad) {
         a.wr[l] = b->mWT[l];
     }
     a.eb = b->sEb;
+    a.xin = b->mXb;
     a.X = c->X; a.theta = theta; a.Y = c->Y; a.Z = c->Z;
     a.G = (uint32_t*)b->G; a.G_words = b->G_stride / 2; a.scratch = (uint32_t*)b->scratch;
     a.for_grad = for_grad ? 1 : 0;

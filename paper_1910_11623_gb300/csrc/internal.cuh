@@ -1,5 +1,6 @@
 // Internal definitions shared by the translation units of libfbsde.
 #pragma once
+#include <cuda_bf16.h>
 #include <cuda_runtime.h>
 #include <stdint.h>
 
@@ -93,6 +94,11 @@ struct fbsde_ctx {
     float* fscal = nullptr;    // device float scalars (projection scales)
     int* nonfinite = nullptr;  // set when a loss/gradient entry is NaN/Inf
     float* gradbuf = nullptr;  // gradient of fbsde_train_step [num_params]
+    // BF16 operand copies of X and V written by the path and seed kernels for
+    // the fused tensor-core kernels (rows of ld_op; NULL in the other forms)
+    __nv_bfloat16* Xb_op = nullptr;
+    __nv_bfloat16* Vb_op = nullptr;
+    int ld_op = 0;
     fbsde::Fp32Work f32{};
     fbsde::Profiler prof;
     uint64_t n_launch = 0;     // kernels launched by this context

@@ -10,6 +10,7 @@
 // per-path scratch for the FP64 loss terms before their fixed-order sum.  Here
 // that scratch is a file-scope device array of a fixed size, reserved on every
 // GPU that loads the library for as long as the process lives.
+#include <cuda_bf16.h>
 #include <cuda_runtime.h>
 
 #include <cmath>
@@ -29,7 +30,8 @@ static __device__ __align__(256) double g_noalloc_path_loss[kNoAllocMaxPaths];
 // The per-path residual and seed kernel of the allocating path (paths.cu).
 __global__ void k_seeds(ProblemDev pd, const float* __restrict__ X, const float* __restrict__ dW,
                         const float* __restrict__ Y, const float* __restrict__ Z, float* __restrict__ alpha,
-                        float* __restrict__ V, double* __restrict__ path_loss);
+                        float* __restrict__ V, double* __restrict__ path_loss, __nv_bfloat16* __restrict__ Vb,
+                        int ldb);
 
 // Fixed-order sum of the M per-path terms held in the array (one block), and
 // Y_0 = Y[0].  Every term read here was written by this call's k_seeds.
@@ -110,7 +112,8 @@ extern "C" fbsde_status fbsde_residual_loss_noalloc(const fbsde_problem* problem
     pd.r = (float)problem->r; pd.sigma = (float)problem->sigma; pd.tgt = problem->terminal_grad_term;
     cudaStream_t st = (cudaStream_t)cuda_stream;
     const int wpb = 8;
-    k_seeds<<<(pd.M + wpb - 1) / wpb, 32 * wpb, 0, st>>>(pd, X_dev, dW_dev, Y_dev, Z_dev, alpha_dev, V_dev, scratch);
+    k_seeds<<<(pd.M + wpb - 1) / wpb, 32 * wpb, 0, st>>>(pd, X_dev, dW_dev, Y_dev, Z_dev, alpha_dev, V_dev, scratch,
+                                                         nullptr, 0);
     e = cudaGetLastError();
     if (e == cudaSuccess) {
         k_noalloc_loss_reduce<<<1, 1024, 0, st>>>(scratch, pd.M, Y_dev, loss_dev, y0_dev);

@@ -6,6 +6,8 @@
 //     (Section 2.2, Eq. "loss"), with a fixed-order loss reduction.
 #include <cuda_runtime.h>
 
+#include <cuda_bf16.h>
+
 #include "internal.cuh"
 #include "philox.cuh"
 
@@ -15,7 +17,8 @@ namespace fbsde {
 // drawing Delta W_n from Philox counter (q, n, m, iter) and updating
 // X_{n+1} = X_n + sigma(X_n) Delta W_n.  Layout: row n * M + m, column d.
 __global__ void k_paths(ProblemDev pd, const float* __restrict__ x0, uint32_t k0, uint32_t k1,
-                        uint32_t it, float* __restrict__ X, float* __restrict__ dW) {
+                        uint32_t it, float* __restrict__ X, float* __restrict__ dW,
+                        __nv_bfloat16* __restrict__ Xb, int ldb) {
     const int Q = (pd.D + 3) >> 2;
     const long idx = (long)blockIdx.x * blockDim.x + threadIdx.x;
     if (idx >= (long)pd.M * Q) return;
@@ -28,6 +31,10 @@ __global__ void k_paths(ProblemDev pd, const float* __restrict__ x0, uint32_t k0
     if (X) {
         float* row = X + (size_t)m * pd.D + d0;
         for (int j = 0; j < nd; ++j) row[j] = x[j];
+    }
+    if (Xb) {
+        __nv_bfloat16* row = Xb + (size_t)m * ldb + d0;
+        for (int j = 0; j < nd; ++j) row[j] = __float2bfloat16_rn(x[j]);
     }
     const float sqrt2 = 1.41421356237309515f;
     for (int n = 0; n < pd.N; ++n) {
@@ -51,6 +58,10 @@ __global__ void k_paths(ProblemDev pd, const float* __restrict__ x0, uint32_t k0
             float* row = X + ((size_t)(n + 1) * pd.M + m) * pd.D + d0;
             for (int j = 0; j < nd; ++j) row[j] = x[j];
         }
+        if (Xb) {
+            __nv_bfloat16* row = Xb + ((size_t)(n + 1) * pd.M + m) * ldb + d0;
+            for (int j = 0; j < nd; ++j) row[j] = __float2bfloat16_rn(x[j]);
+        }
     }
 }
 
@@ -62,7 +73,7 @@ fbsde_status launch_paths(fbsde_ctx* ctx, uint64_t iter) {
     const int tok = prof_begin(ctx, PROF_OTHER);
     k_paths<<<(unsigned)((n + bs - 1) / bs), bs, 0, ctx->stream>>>(
         pd, ctx->x0_dev, (uint32_t)ctx->seed, (uint32_t)(ctx->seed >> 32), (uint32_t)iter, ctx->X,
-        ctx->dW);
+        ctx->dW, ctx->Xb_op, ctx->ld_op);
     prof_end(ctx, PROF_OTHER, tok, 0.0);
     FBSDE_CK_LAUNCH(ctx);
     return FBSDE_OK;
@@ -142,7 +153,7 @@ __device__ __forceinline__ float warp_sum(float v) {
 __global__ void k_seeds(ProblemDev pd, const float* __restrict__ X, const float* __restrict__ dW,
                         const float* __restrict__ Y, const float* __restrict__ Z,
                         float* __restrict__ alpha, float* __restrict__ V,
-                        double* __restrict__ path_loss) {
+                        double* __restrict__ path_loss, __nv_bfloat16* __restrict__ Vb, int ldb) {
     const int lane = threadIdx.x & 31;
     const int m = (int)(((long)blockIdx.x * blockDim.x + threadIdx.x) >> 5);
     if (m >= pd.M) return;
@@ -175,6 +186,7 @@ __global__ void k_seeds(ProblemDev pd, const float* __restrict__ X, const float*
             const float sdw = bsb ? pd.sigma * x[d] * dw[d] : sqrt2 * dw[d];
             const float phiz = bsb ? -pd.r * x[d] : 2.f * z[d];
             vp[d] = -2.f * r * (phiz * pd.dt + sdw);
+            if (Vb) Vb[p * ldb + d] = __float2bfloat16_rn(vp[d]);
         }
         rprev = r;
     }
@@ -199,6 +211,7 @@ __global__ void k_seeds(ProblemDev pd, const float* __restrict__ X, const float*
             zt = fmaf(diff, diff, zt);
         }
         vp[d] = v;
+        if (Vb) Vb[p * ldb + d] = __float2bfloat16_rn(v);
     }
     zt = warp_sum(zt);
     if (pd.tgt) pl += (double)zt;
@@ -247,7 +260,7 @@ fbsde_status launch_seeds(fbsde_ctx* ctx, float* loss_dev, float* y0_dev) {
     const int wpb = 8;  // warps per block
     const int tok = prof_begin(ctx, PROF_OTHER);
     k_seeds<<<(pd.M + wpb - 1) / wpb, 32 * wpb, 0, ctx->stream>>>(
-        pd, ctx->X, ctx->dW, ctx->Y, ctx->Z, ctx->alpha, ctx->V, ctx->path_loss_d);
+        pd, ctx->X, ctx->dW, ctx->Y, ctx->Z, ctx->alpha, ctx->V, ctx->path_loss_d, ctx->Vb_op, ctx->ld_op);
     FBSDE_CK_LAUNCH(ctx);
     k_loss_reduce<<<1, 1024, 0, ctx->stream>>>(ctx->path_loss_d, pd.M, ctx->Y, loss_dev, y0_dev,
                                                ctx->nonfinite);

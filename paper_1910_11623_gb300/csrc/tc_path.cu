@@ -180,6 +180,11 @@ fbsde_status bf16_create(fbsde_ctx* c) {
         ok &= map3d(&b->sEb, b->Eb[0], b->wp, P64, (uint64_t)L + 1, b->wp, b->OP_stride, 128);
     }
     if (!ok) return set_err(c, FBSDE_ERR_CUDA, "cuTensorMapEncodeTiled failed (driver entry point or arguments)");
+    if (b->fused) {
+        c->Xb_op = b->Xb;
+        c->Vb_op = b->Vb;
+        c->ld_op = b->Dp;
+    }
     return FBSDE_OK;
 }
 
@@ -380,29 +385,61 @@ __global__ void __launch_bounds__(256) k_colsum(size_t P, int ncols, const T* __
     for (int cb = 0; cb < ncols; cb += 256) {
         float acc[8] = {0.f, 0.f, 0.f, 0.f, 0.f, 0.f, 0.f, 0.f};
         const int c0 = cb + tx * 8;
-        for (size_t p = p0 + ty; p < p1; p += 8) {
-            const float wt = mode == 0 ? 1.f : mode == 1 ? (float)(p / M) * dt : wts[p];
-            const T* row = X + p * ldx;
-            if (vec) {
-                if (c0 < ncols) {
-                    float v[8];
+        if (vec && c0 < ncols) {
+            // four rows in flight per thread
+            size_t p = p0 + ty;
+            for (; p + 24 < p1; p += 32) {
+                float v[4][8];
+#pragma unroll
+                for (int u = 0; u < 4; ++u) {
+                    const T* row = X + (p + 8 * u) * ldx;
                     if (sizeof(T) == 2) {
-                        const uint4 u = *reinterpret_cast<const uint4*>(row + c0);
-                        const uint32_t w4[4] = {u.x, u.y, u.z, u.w};
+                        const uint4 q = *reinterpret_cast<const uint4*>(row + c0);
+                        const uint32_t w4[4] = {q.x, q.y, q.z, q.w};
 #pragma unroll
                         for (int i = 0; i < 4; ++i) {
                             const float2 f = __bfloat1622float2(*reinterpret_cast<const __nv_bfloat162*>(&w4[i]));
-                            v[2 * i] = f.x; v[2 * i + 1] = f.y;
+                            v[u][2 * i] = f.x; v[u][2 * i + 1] = f.y;
                         }
                     } else {
                         const float4 a = reinterpret_cast<const float4*>(row + c0)[0];
                         const float4 b = reinterpret_cast<const float4*>(row + c0)[1];
-                        v[0] = a.x; v[1] = a.y; v[2] = a.z; v[3] = a.w; v[4] = b.x; v[5] = b.y; v[6] = b.z; v[7] = b.w;
+                        v[u][0] = a.x; v[u][1] = a.y; v[u][2] = a.z; v[u][3] = a.w;
+                        v[u][4] = b.x; v[u][5] = b.y; v[u][6] = b.z; v[u][7] = b.w;
                     }
-#pragma unroll
-                    for (int i = 0; i < 8; ++i) acc[i] = fmaf(wt, v[i], acc[i]);
                 }
-            } else {
+#pragma unroll
+                for (int u = 0; u < 4; ++u) {
+                    const size_t pu = p + 8 * u;
+                    const float wt = mode == 0 ? 1.f : mode == 1 ? (float)(pu / M) * dt : wts[pu];
+#pragma unroll
+                    for (int i = 0; i < 8; ++i) acc[i] = fmaf(wt, v[u][i], acc[i]);
+                }
+            }
+            for (; p < p1; p += 8) {
+                const float wt = mode == 0 ? 1.f : mode == 1 ? (float)(p / M) * dt : wts[p];
+                const T* row = X + p * ldx;
+                float v[8];
+                if (sizeof(T) == 2) {
+                    const uint4 q = *reinterpret_cast<const uint4*>(row + c0);
+                    const uint32_t w4[4] = {q.x, q.y, q.z, q.w};
+#pragma unroll
+                    for (int i = 0; i < 4; ++i) {
+                        const float2 f = __bfloat1622float2(*reinterpret_cast<const __nv_bfloat162*>(&w4[i]));
+                        v[2 * i] = f.x; v[2 * i + 1] = f.y;
+                    }
+                } else {
+                    const float4 a = reinterpret_cast<const float4*>(row + c0)[0];
+                    const float4 b = reinterpret_cast<const float4*>(row + c0)[1];
+                    v[0] = a.x; v[1] = a.y; v[2] = a.z; v[3] = a.w; v[4] = b.x; v[5] = b.y; v[6] = b.z; v[7] = b.w;
+                }
+#pragma unroll
+                for (int i = 0; i < 8; ++i) acc[i] = fmaf(wt, v[i], acc[i]);
+            }
+        } else if (!vec) {
+            for (size_t p = p0 + ty; p < p1; p += 8) {
+                const float wt = mode == 0 ? 1.f : mode == 1 ? (float)(p / M) * dt : wts[p];
+                const T* row = X + p * ldx;
 #pragma unroll
                 for (int i = 0; i < 8; ++i)
                     if (c0 + i < ncols) acc[i] = fmaf(wt, (float)row[c0 + i], acc[i]);
@@ -422,24 +459,40 @@ __global__ void __launch_bounds__(256) k_colsum(size_t P, int ncols, const T* __
     }
 }
 
+// One warp per column: lane i sums splits i, i+32, ... in order, then a fixed
+// butterfly combines the lanes (bit-reproducible).
 __global__ void k_colsum_reduce(const float* __restrict__ part, int splits, int ncols, float* __restrict__ out,
                                 int ldo, int accumulate) {
-    const int c = blockIdx.x * blockDim.x + threadIdx.x;
+    const int c = (int)(((size_t)blockIdx.x * blockDim.x + threadIdx.x) >> 5);
+    const int lane = threadIdx.x & 31;
     if (c >= ncols) return;
     float s = 0.f;
-    for (int k = 0; k < splits; ++k) s += part[(size_t)k * ncols + c];
-    out[(size_t)c * ldo] = accumulate ? out[(size_t)c * ldo] + s : s;
+    for (int k = lane; k < splits; k += 32) s += part[(size_t)k * ncols + c];
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) s += __shfl_xor_sync(0xffffffffu, s, o);
+    if (lane == 0) out[(size_t)c * ldo] = accumulate ? out[(size_t)c * ldo] + s : s;
 }
 
-// out[r * ld + off + c] = sum_z part[z][r][c] for c < nc (fixed order)
+// out[r * ld + off + c] = sum_z part[z][r][c] for c < nc: thread per output,
+// splits summed in order with four independent partial sums combined in a
+// fixed order (bit-reproducible).
 __global__ void k_reduce_split(const float* __restrict__ part, int splits, int rows, int N, int nc,
                                float* __restrict__ out, int ld, int off) {
     const int i = blockIdx.x * blockDim.x + threadIdx.x;
     if (i >= rows * nc) return;
     const int r = i / nc, cc = i % nc;
-    float s = 0.f;
-    for (int z = 0; z < splits; ++z) s += part[((size_t)z * rows + r) * N + cc];
-    out[(size_t)r * ld + off + cc] = s;
+    const size_t stride = (size_t)rows * N;
+    const float* q = part + (size_t)r * N + cc;
+    float s0 = 0.f, s1 = 0.f, s2 = 0.f, s3 = 0.f;
+    int z = 0;
+    for (; z + 3 < splits; z += 4) {
+        s0 += q[(size_t)z * stride];
+        s1 += q[(size_t)(z + 1) * stride];
+        s2 += q[(size_t)(z + 2) * stride];
+        s3 += q[(size_t)(z + 3) * stride];
+    }
+    for (; z < splits; ++z) s0 += q[(size_t)z * stride];
+    out[(size_t)r * ld + off + cc] = (s0 + s1) + (s2 + s3);
 }
 
 // ------------------------------------------------------------------ launch helpers
@@ -480,7 +533,8 @@ static fbsde_status colsum(fbsde_ctx* c, int cls, const void* X, bool is_bf16, i
     else
         k_colsum<float><<<splits, 256, 0, c->stream>>>(P, ncols, (const float*)X, ldx, mode, wts, c->M, dt, b->colpart, chunk);
     FBSDE_CK_LAUNCH(c);
-    k_colsum_reduce<<<nblk(ncols, 128), 128, 0, c->stream>>>(b->colpart, splits, ncols, out, ldo, accumulate);
+    k_colsum_reduce<<<nblk((size_t)ncols * 32, 256), 256, 0, c->stream>>>(b->colpart, splits, ncols, out, ldo,
+                                                                        accumulate);
     prof_end(c, cls, tok, 2.0 * (double)P * ncols);
     FBSDE_CK_LAUNCH(c);
     return FBSDE_OK;
