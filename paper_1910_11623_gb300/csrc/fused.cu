@@ -41,8 +41,14 @@ namespace fbsde {
 
 constexpr uint32_t kFStageBytes = 32768;  // one weight slice: up to 256 rows x 128 B
 constexpr uint32_t kFTileBytes = 65536;   // activation tile: 4 x [128 x 64] BF16
-constexpr int kFThreads = 320;
-constexpr int kFEpiThreads = 256;
+// Epilogue warp groups (4 warps each, one thread per TMEM lane per group) of
+// the two kernels; each SM sub-partition holds 16K registers, so the forward
+// kernel (3 groups, 14 warps) stays within 128 registers per thread and the
+// backward kernel (2 groups) within 168.
+constexpr int kFwdGroups = 3;
+constexpr int kBwdGroups = 2;
+constexpr int kFDepth = 4;  // chunks of global operands kept in flight per thread
+__host__ __device__ constexpr int fused_threads(int groups) { return 64 + 128 * groups; }
 constexpr int kFwdStages = 4;
 constexpr int kBwdStages = 2;
 
@@ -106,6 +112,19 @@ __device__ __forceinline__ void tmem_st_f16(uint32_t taddr, const float* v) {
     tc::tmem_st16(taddr, u);
 }
 
+__device__ __forceinline__ void tmem_st_f8(uint32_t taddr, const float* v) {
+    uint32_t u[8];
+#pragma unroll
+    for (int j = 0; j < 8; ++j) u[j] = __float_as_uint(v[j]);
+    tc::tmem_st8(taddr, u);
+}
+__device__ __forceinline__ void st_bf16x8(bf16* dst, const float* v) {
+    uint4 u;
+    u.x = pack_bf16x2(v[0], v[1]); u.y = pack_bf16x2(v[2], v[3]);
+    u.z = pack_bf16x2(v[4], v[5]); u.w = pack_bf16x2(v[6], v[7]);
+    *reinterpret_cast<uint4*>(dst) = u;
+}
+
 // Column-pair-major 128-row blocks (per-CTA scratch, g_l): the BF16 pair of
 // columns (2k, 2k+1) of row r is 32-bit word k * 128 + r, so the 32 rows of a
 // warp touch one 128-byte line per access instead of 32 lines.
@@ -119,11 +138,53 @@ __device__ __forceinline__ void ld_pm16_raw(const uint32_t* blk, int row, int c0
 #pragma unroll
     for (int k = 0; k < 8; ++k) u[k] = q[k * 128];
 }
+__device__ __forceinline__ void st_pm8(uint32_t* blk, int row, int c0, const float* v) {
+    uint32_t* q = blk + (c0 >> 1) * 128 + row;
+#pragma unroll
+    for (int k = 0; k < 4; ++k) q[k * 128] = pack_bf16x2(v[2 * k], v[2 * k + 1]);
+}
+__device__ __forceinline__ void ld_pm8_raw(const uint32_t* blk, int row, int c0, uint32_t (&u)[4]) {
+    const uint32_t* q = blk + (c0 >> 1) * 128 + row;
+#pragma unroll
+    for (int k = 0; k < 4; ++k) u[k] = q[k * 128];
+}
+__device__ __forceinline__ void unpack8(const uint32_t (&u)[4], float* v) {
+#pragma unroll
+    for (int k = 0; k < 4; ++k) {
+        const float2 f = unpack_bf16x2(u[k]);
+        v[2 * k] = f.x; v[2 * k + 1] = f.y;
+    }
+}
 __device__ __forceinline__ void unpack16(const uint32_t (&u)[8], float* v) {
 #pragma unroll
     for (int k = 0; k < 8; ++k) {
         const float2 f = unpack_bf16x2(u[k]);
         v[2 * k] = f.x; v[2 * k + 1] = f.y;
+    }
+}
+
+// Walk the chunks first, first + step, ... < n with the global operands of the
+// next kFDepth chunks in flight: load(ch, words) issues the loads of chunk ch,
+// body(ch, words) consumes them.  Register indices stay static (unrolled).
+template <int NW, class Load, class Body, int DEPTH = kFDepth>
+__device__ __forceinline__ void chunk_loop(int first, int step, int n, Load load, Body body) {
+    uint32_t buf[DEPTH][NW];
+#pragma unroll
+    for (int d = 0; d < DEPTH; ++d)
+        if (first + d * step < n) load(first + d * step, buf[d]);
+    for (int base = 0; first + base * step < n; base += DEPTH) {
+#pragma unroll
+        for (int d = 0; d < DEPTH; ++d) {
+            const int ch = first + (base + d) * step;
+            if (ch < n) {
+                uint32_t cur[NW];
+#pragma unroll
+                for (int k = 0; k < NW; ++k) cur[k] = buf[d][k];
+                const int nxt = ch + DEPTH * step;
+                if (nxt < n) load(nxt, buf[d]);
+                body(ch, cur);
+            }
+        }
     }
 }
 
@@ -135,7 +196,7 @@ __device__ __forceinline__ void unpack16(const uint32_t (&u)[8], float* v) {
 // the stores of this phase.  Both waits are bounded.
 struct StoreSync {
     uint64_t* tfree;  // count 1: the storing thread
-    uint64_t* wdone;  // count 256: every epilogue thread
+    uint64_t* wdone;  // count: every epilogue thread
     bool st_thread;
     uint32_t phase;
     __device__ bool before_write() {
@@ -145,10 +206,18 @@ struct StoreSync {
         }
         return tc::mbar_wait(tfree, phase & 1u, tc::kWaitBudget);
     }
-    // returns false on timeout; the storing thread may issue stores after it
-    __device__ bool after_write() {
+    // returns false on timeout; the storing thread may issue stores after it.
+    // With `aready`, every thread also hands the tiles to the MMA issuer
+    // before the storing thread waits, so the next contraction does not wait
+    // for the stores to be issued (both only read the tiles).
+    __device__ bool after_write(uint64_t* aready = nullptr) {
         tc::fence_async_shared();
         tc::mbar_arrive(wdone);
+        if (aready) {
+            tc::tmem_wait_st();
+            tc::tc_fence_before();
+            tc::mbar_arrive(aready);
+        }
         bool ok = true;
         if (st_thread) ok = tc::mbar_wait(wdone, phase & 1u, tc::kWaitBudget);
         ++phase;
@@ -222,6 +291,7 @@ __device__ void mma_role(const Sched& sch, int ntiles, int nstages, uint32_t aba
             }
             tc::tc_fence_after();
             const FGemm g = sch.gemm(q);
+            sch.prefetch(q, t);
             const uint32_t abase = g.asel ? abase1 : abase0;
             const uint32_t idesc = tc::idesc_bf16(128, g.N, 0, 0);
             const bool dual = g.dual != 0;
@@ -251,33 +321,6 @@ __device__ void mma_role(const Sched& sch, int ntiles, int nstages, uint32_t aba
     if (!ok) {
         if (err) atomicExch(err, 2);
         *abort_flag = 1;
-    }
-}
-
-// Epilogue threads: hand contraction q's operand over to the MMA issuer.
-__device__ __forceinline__ void epi_handoff(uint64_t* aready) {
-    tc::tmem_wait_st();
-    tc::fence_async_shared();
-    tc::tc_fence_before();
-    tc::mbar_arrive(aready);
-}
-
-// Load a [128 x ncols] FP32 row block (row p of X, zero beyond P or ncols) into
-// a BF16 tile, and optionally copy it to a BF16 global row of width ldo.
-__device__ __forceinline__ void load_input_tile(uint8_t* tile, const float* src, int p, bool valid, int ncols,
-                                                int ncols_pad, int row, int eg, bf16* gcopy, int ldo) {
-    for (int u = eg; u < ncols_pad / 8; u += 2) {
-        const int c = u * 8;
-        float v[8];
-#pragma unroll
-        for (int j = 0; j < 8; ++j) v[j] = (valid && c + j < ncols) ? __ldg(src + (size_t)p * ncols + c + j) : 0.f;
-        st_tile8(tile, row, c, v);
-        if (gcopy && valid) {
-            uint4 u4;
-            u4.x = pack_bf16x2(v[0], v[1]); u4.y = pack_bf16x2(v[2], v[3]);
-            u4.z = pack_bf16x2(v[4], v[5]); u4.w = pack_bf16x2(v[6], v[7]);
-            *reinterpret_cast<uint4*>(gcopy + (size_t)p * ldo + c) = u4;
-        }
     }
 }
 
@@ -317,10 +360,20 @@ struct FwdZSched {
         else { g.map = &a->wr[0]; g.nk = a->wp / 64; g.K = a->w; g.N = a->Dn; }
         return g;
     }
+    // into L2 while contraction q runs: the act' block its epilogue reads
+    __device__ void prefetch(int q, int) const {
+        const int L = a->L;
+        if (q > L && q <= 2 * L) {
+            const int l = 2 * L + 1 - q;
+            const size_t blk = (size_t)(a->w / 2) * 128;
+            tc::prefetch_l2_bulk(a->scratch + ((size_t)blockIdx.x * L + (l - 1)) * blk, (uint32_t)(blk * 4));
+        }
+    }
 };
 
 template <int ACT, bool RES>
-__global__ void __launch_bounds__(kFThreads, 1) k_fused_fwdz(const __grid_constant__ FwdZArgs a) {
+__global__ void __launch_bounds__(fused_threads(kFwdGroups), 1) k_fused_fwdz(const __grid_constant__ FwdZArgs a) {
+    constexpr int NG = kFwdGroups, NE = 128 * NG;
     extern __shared__ uint8_t smem_raw[];
     uint8_t* smem = (uint8_t*)(((uintptr_t)smem_raw + 1023) & ~(uintptr_t)1023);
     uint8_t* tile = smem;
@@ -333,8 +386,10 @@ __global__ void __launch_bounds__(kFThreads, 1) k_fused_fwdz(const __grid_consta
     uint64_t* tfree = aready + 1;
     uint64_t* wdone = tfree + 1;
     uint64_t* xfull = wdone + 1;
-    uint32_t* tslot = (uint32_t*)(xfull + 1);
+    uint64_t* ybar = xfull + 1;
+    uint32_t* tslot = (uint32_t*)(ybar + 1);
     volatile int* abort_flag = (volatile int*)(tslot + 1);
+    float* ysum = (float*)(smem + kFTileBytes + kFwdStages * kFStageBytes) + (a.L + 3) * a.w + 64;
 
     const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
     const int L = a.L;
@@ -347,10 +402,11 @@ __global__ void __launch_bounds__(kFThreads, 1) k_fused_fwdz(const __grid_consta
             tc::mbar_init(&bempty[s], 1);
         }
         tc::mbar_init(accf, 1);
-        tc::mbar_init(aready, kFEpiThreads);
+        tc::mbar_init(aready, NE);
         tc::mbar_init(tfree, 1);
-        tc::mbar_init(wdone, kFEpiThreads);
+        tc::mbar_init(wdone, NE);
         tc::mbar_init(xfull, 1);
+        tc::mbar_init(ybar, NE);
         *abort_flag = 0;
         tc::fence_mbar_init();
     }
@@ -370,8 +426,8 @@ __global__ void __launch_bounds__(kFThreads, 1) k_fused_fwdz(const __grid_consta
             mma_role(sch, a.ntiles, kFwdStages, tc::smem_u32(tile), tc::smem_u32(tile), tc::smem_u32(ring), tmem,
                      bfull, bempty, accf, aready, abort_flag, a.err);
     } else {
-        const int eg = (warp - 2) >> 2;
-        const int lg = warp & 3;
+        const int eg = (warp - 2) >> 2;  // epilogue group: chunks eg, eg + NG, ...
+        const int lg = warp & 3;         // TMEM lane group of this warp
         const int row = lg * 32 + lane;
         const uint32_t tacc = tmem + ((uint32_t)(lg * 32) << 16);
         const uint32_t tres = tacc + 256u;
@@ -382,6 +438,7 @@ __global__ void __launch_bounds__(kFThreads, 1) k_fused_fwdz(const __grid_consta
         StoreSync ss{tfree, wdone, warp == 2 && lane == 0, 0u};
         const int nq = sch.nq();
         const int nkw = a.wp / 64;
+        const int nch = a.w / 8;
         int qg = 0, tcount = 0;
         bool ok = true;
         for (int t = blockIdx.x; t < a.ntiles && ok; t += gridDim.x) {
@@ -397,9 +454,7 @@ __global__ void __launch_bounds__(kFThreads, 1) k_fused_fwdz(const __grid_consta
             }
             if (!tc::mbar_wait(xfull, (uint32_t)tcount & 1u, tc::kWaitBudget)) { ok = false; break; }
             ++tcount;
-            if (!ss.after_write()) { ok = false; break; }
-            tc::tc_fence_before();
-            tc::mbar_arrive(aready);
+            if (!ss.after_write(aready)) { ok = false; break; }
             for (int q = 0; q < nq; ++q, ++qg) {
                 if (!tc::mbar_wait(accf, (uint32_t)qg & 1u, tc::kWaitBudget)) {
                     ok = false;
@@ -415,15 +470,15 @@ __global__ void __launch_bounds__(kFThreads, 1) k_fused_fwdz(const __grid_consta
                     const float* bias = ptab + l * a.w;
                     uint32_t* sc = scr + (size_t)l * blk;
                     float ypart = 0.f;
-                    for (int ch = eg; ch < a.w / 16; ch += 2) {
-                        const int c0 = ch * 16;
-                        uint32_t rv[16], rr[16];
-                        tc::tmem_ld16(tacc + (uint32_t)c0, rv);
-                        if (RES && l >= 1) tc::tmem_ld16(tres + (uint32_t)c0, rr);
+                    for (int ch = eg; ch < nch; ch += NG) {
+                        const int c0 = ch * 8;
+                        uint32_t rv[8], rr[8];
+                        tc::tmem_ld8(tacc + (uint32_t)c0, rv);
+                        if (RES && l >= 1) tc::tmem_ld8(tres + (uint32_t)c0, rr);
                         tc::tmem_wait_ld();
-                        float h[16], d1[16];
+                        float h[8], d1[8];
 #pragma unroll
-                        for (int j = 0; j < 16; ++j) {
+                        for (int j = 0; j < 8; ++j) {
                             float av = __uint_as_float(rv[j]) + bias[c0 + j];
                             if (l == 0) av = fmaf(tval, win0[c0 + j], av);
                             const Act3 f = act3_sfu<ACT>(av);
@@ -432,73 +487,79 @@ __global__ void __launch_bounds__(kFThreads, 1) k_fused_fwdz(const __grid_consta
                         }
                         if (l < L) {
                             st_tile8(tile, row, c0, h);
-                            st_tile8(tile, row, c0 + 8, h + 8);
-                            st_pm16(sc, row, c0, d1);
-                            if (RES) tmem_st_f16(tres + (uint32_t)c0, h);
+                            st_pm8(sc, row, c0, d1);
+                            if (RES) tmem_st_f8(tres + (uint32_t)c0, h);
                         } else {
                             // top: y = w_o^T h_L + b_o and e_L = act'(a_L) w_o
-                            float e[16];
+                            float e[8];
 #pragma unroll
-                            for (int j = 0; j < 16; ++j) {
+                            for (int j = 0; j < 8; ++j) {
                                 ypart = fmaf(h[j], wo[c0 + j], ypart);
                                 e[j] = d1[j] * wo[c0 + j];
                             }
                             st_tile8(tile, row, c0, e);
-                            st_tile8(tile, row, c0 + 8, e + 8);
                         }
                     }
-                    // the two groups' partial sums commute exactly: deterministic
-                    if (l == L && valid) atomicAdd(a.Y + p, ypart + (eg == 0 ? __ldg(a.theta + a.off.bo) : 0.f));
-                    if (l == L) store_layer = L;
+                    if (l == L) {
+                        // y = b_o + the groups' partial sums, added in a fixed order
+                        ysum[eg * 128 + row] = ypart;
+                        tc::mbar_arrive(ybar);
+                        if (eg == 0) {
+                            if (!tc::mbar_wait(ybar, (uint32_t)(tcount - 1) & 1u, tc::kWaitBudget)) { ok = false; break; }
+                            float y = __ldg(a.theta + a.off.bo);
+                            for (int g2 = 0; g2 < NG; ++g2) y += ysum[g2 * 128 + row];
+                            if (valid) a.Y[p] = y;
+                        }
+                        store_layer = L;
+                    }
                 } else if (q <= 2 * L) {
                     // reverse through layer l: g_{l-1} = [g_l] + W_l^T e_l, e_{l-1} = act'(a_{l-1}) g_{l-1}
                     const int l = 2 * L + 1 - q;
                     const uint32_t* sc = scr + (size_t)(l - 1) * blk;
                     uint32_t* gout = gtile + (size_t)(l - 1) * a.G_words;
-                    for (int ch = eg; ch < a.w / 16; ch += 2) {
-                        const int c0 = ch * 16;
-                        uint32_t du[8];
-                        ld_pm16_raw(sc, row, c0, du);
-                        uint32_t rv[16], rr[16];
-                        tc::tmem_ld16(tacc + (uint32_t)c0, rv);
-                        if (RES && l < L) tc::tmem_ld16(tres + (uint32_t)c0, rr);
-                        tc::tmem_wait_ld();
-                        float d1[16], g[16], e[16];
-                        unpack16(du, d1);
+                    chunk_loop<4>(eg, NG, nch,
+                        [&](int ch, uint32_t (&u)[4]) { ld_pm8_raw(sc, row, ch * 8, u); },
+                        [&](int ch, const uint32_t (&du)[4]) {
+                            const int c0 = ch * 8;
+                            float d1[8];
+                            unpack8(du, d1);
+                            uint32_t rv[8], rr[8];
+                            tc::tmem_ld8(tacc + (uint32_t)c0, rv);
+                            if (RES && l < L) tc::tmem_ld8(tres + (uint32_t)c0, rr);
+                            tc::tmem_wait_ld();
+                            float g[8], e[8];
 #pragma unroll
-                        for (int j = 0; j < 16; ++j) {
-                            const float gl = RES ? (l == L ? wo[c0 + j] : __uint_as_float(rr[j])) : 0.f;
-                            g[j] = gl + __uint_as_float(rv[j]);
-                            e[j] = d1[j] * g[j];
-                        }
-                        if (a.for_grad) st_pm16(gout, row, c0, g);
-                        st_tile8(tile, row, c0, e);
-                        st_tile8(tile, row, c0 + 8, e + 8);
-                        if (RES) tmem_st_f16(tres + (uint32_t)c0, g);
-                    }
+                            for (int j = 0; j < 8; ++j) {
+                                const float gl = RES ? (l == L ? wo[c0 + j] : __uint_as_float(rr[j])) : 0.f;
+                                g[j] = gl + __uint_as_float(rv[j]);
+                                e[j] = d1[j] * g[j];
+                            }
+                            if (a.for_grad) st_pm8(gout, row, c0, g);
+                            st_tile8(tile, row, c0, e);
+                            if (RES) tmem_st_f8(tres + (uint32_t)c0, g);
+                        });
                     store_layer = l - 1;
                 } else {
                     // Z = W_in[:,1:]^T e_0
-                    for (int ch = eg; ch < a.Dn / 16; ch += 2) {
-                        const int c0 = ch * 16;
-                        uint32_t rv[16];
-                        tc::tmem_ld16(tacc + (uint32_t)c0, rv);
+                    for (int ch = eg; ch < a.Dn / 8; ch += NG) {
+                        const int c0 = ch * 8;
+                        uint32_t rv[8];
+                        tc::tmem_ld8(tacc + (uint32_t)c0, rv);
                         tc::tmem_wait_ld();
                         if (valid) {
 #pragma unroll
-                            for (int j = 0; j < 16; ++j)
+                            for (int j = 0; j < 8; ++j)
                                 if (c0 + j < a.D) a.Z[(size_t)p * a.D + c0 + j] = __uint_as_float(rv[j]);
                         }
                     }
                 }
                 if (writes_tile) {
-                    if (!ss.after_write()) { ok = false; break; }
+                    if (!ss.after_write(q < nq - 1 ? aready : nullptr)) { ok = false; break; }
                     if (ss.st_thread && a.for_grad && store_layer >= 0) {
                         for (int k = 0; k < nkw; ++k) tc::tma_store_3d(&a.eb, tile + k * 16384, k * 64, t * 128, store_layer);
                         tc::tma_store_commit();
                     }
-                }
-                if (q < nq - 1) {
+                } else if (q < nq - 1) {
                     tc::tmem_wait_st();
                     tc::tc_fence_before();
                     tc::mbar_arrive(aready);
@@ -567,13 +628,27 @@ struct BwdSched {
         }
         return g;
     }
+    // into L2 while contraction q runs: the blocks its epilogue reads
+    __device__ void prefetch(int q, int t) const {
+        const int L = a->L;
+        const size_t blk = (size_t)(a->w / 2) * 128;
+        if (q < L) {
+            tc::prefetch_l2_bulk(a->G + (size_t)q * a->G_words + (size_t)t * blk, (uint32_t)(blk * 4));
+        } else if (q > L) {
+            const int l = L - (q - (L + 1));
+            const uint32_t* d1 = a->scratch + (size_t)blockIdx.x * 2 * L * blk + (size_t)(l - 1) * blk;
+            tc::prefetch_l2_bulk(d1, (uint32_t)(blk * 4));
+            tc::prefetch_l2_bulk(d1 + (size_t)L * blk, (uint32_t)(blk * 4));
+        }
+    }
 };
 
 // The backward recomputes the forward with the BF16 skip path of the tile (the
 // FP32 residual of k_fused_fwdz has no room here: TMEM holds both the forward
 // and the tangent accumulators), and carries the tangent h' in BF16 as well.
 template <int ACT, bool RES>
-__global__ void __launch_bounds__(kFThreads, 1) k_fused_bwd(const __grid_constant__ BwdArgs a) {
+__global__ void __launch_bounds__(fused_threads(kBwdGroups), 1) k_fused_bwd(const __grid_constant__ BwdArgs a) {
+    constexpr int NG = kBwdGroups, NE = 128 * NG;
     extern __shared__ uint8_t smem_raw[];
     uint8_t* smem = (uint8_t*)(((uintptr_t)smem_raw + 1023) & ~(uintptr_t)1023);
     uint8_t* tile_h = smem;                  // h_l in the up-sweep, abar_l in the down-sweep
@@ -601,9 +676,9 @@ __global__ void __launch_bounds__(kFThreads, 1) k_fused_bwd(const __grid_constan
             tc::mbar_init(&bempty[s], 1);
         }
         tc::mbar_init(accf, 1);
-        tc::mbar_init(aready, kFEpiThreads);
+        tc::mbar_init(aready, NE);
         tc::mbar_init(tfree, 1);
-        tc::mbar_init(wdone, kFEpiThreads);
+        tc::mbar_init(wdone, NE);
         tc::mbar_init(xfull, 1);
         *abort_flag = 0;
         tc::fence_mbar_init();
@@ -636,7 +711,7 @@ __global__ void __launch_bounds__(kFThreads, 1) k_fused_bwd(const __grid_constan
         uint32_t* scr_S = scr_d1 + (size_t)L * blk;                       // S_l, l < L
         StoreSync ss{tfree, wdone, warp == 2 && lane == 0, 0u};
         const int nq = sch.nq();
-        const int nch = a.w / 16;
+        const int nch = a.w / 8;
         const int nkw = a.wp / 64, nkx = a.Dp / 64;
         int qg = 0, tcount = 0;
         bool ok = true;
@@ -657,9 +732,7 @@ __global__ void __launch_bounds__(kFThreads, 1) k_fused_bwd(const __grid_constan
             }
             if (!tc::mbar_wait(xfull, (uint32_t)tcount & 1u, tc::kWaitBudget)) { ok = false; break; }
             ++tcount;
-            if (!ss.after_write()) { ok = false; break; }
-            tc::tc_fence_before();
-            tc::mbar_arrive(aready);
+            if (!ss.after_write(aready)) { ok = false; break; }
             for (int q = 0; q < nq; ++q, ++qg) {
                 if (!tc::mbar_wait(accf, (uint32_t)qg & 1u, tc::kWaitBudget)) {
                     ok = false;
@@ -675,32 +748,27 @@ __global__ void __launch_bounds__(kFThreads, 1) k_fused_bwd(const __grid_constan
                     const int l = q;
                     const float* bias = ptab + l * a.w;
                     const uint32_t* gin = gtile + (size_t)l * a.G_words;
-                    uint32_t gq[8] = {0, 0, 0, 0, 0, 0, 0, 0};
-                    if (l < L && eg < nch) ld_pm16_raw(gin, row, eg * 16, gq);
-                    for (int ch = eg; ch < nch; ch += 2) {
-                        const int c0 = ch * 16;
-                        float g[16];
+                    auto body = [&](int ch, const uint32_t (&gq)[4]) {
+                        const int c0 = ch * 8;
+                        float g[8];
                         if (l < L) {
-                            unpack16(gq, g);
-                            if (ch + 2 < nch) ld_pm16_raw(gin, row, c0 + 32, gq);
+                            unpack8(gq, g);
                         } else {
 #pragma unroll
-                            for (int j = 0; j < 16; ++j) g[j] = wo[c0 + j];
+                            for (int j = 0; j < 8; ++j) g[j] = wo[c0 + j];
                         }
-                        uint32_t rf[16], rt[16];
-                        tc::tmem_ld16(tacc + (uint32_t)c0, rf);
-                        tc::tmem_ld16(tsec + (uint32_t)c0, rt);
-                        float hp[16], hdp[16];
+                        uint32_t rf[8], rt[8];
+                        tc::tmem_ld8(tacc + (uint32_t)c0, rf);
+                        tc::tmem_ld8(tsec + (uint32_t)c0, rt);
+                        float hp[8], hdp[8];
                         if (RES && l >= 1) {
                             ld_tile8(tile_h, row, c0, hp);
-                            ld_tile8(tile_h, row, c0 + 8, hp + 8);
                             ld_tile8(tile_d, row, c0, hdp);
-                            ld_tile8(tile_d, row, c0 + 8, hdp + 8);
                         }
                         tc::tmem_wait_ld();
-                        float h[16], hd[16], d1[16], S[16];
+                        float h[8], hd[8], d1[8], S[8];
 #pragma unroll
-                        for (int j = 0; j < 16; ++j) {
+                        for (int j = 0; j < 8; ++j) {
                             float av = __uint_as_float(rf[j]) + bias[c0 + j];
                             if (l == 0) av = fmaf(tval, win0[c0 + j], av);
                             const Act3 f = act3_sfu<ACT>(av);
@@ -711,26 +779,29 @@ __global__ void __launch_bounds__(kFThreads, 1) k_fused_bwd(const __grid_constan
                             d1[j] = f.d1;
                         }
                         st_tile8(tile_d, row, c0, hd);
-                        st_tile8(tile_d, row, c0 + 8, hd + 8);
                         if (l < L) {
                             st_tile8(tile_h, row, c0, h);
-                            st_tile8(tile_h, row, c0 + 8, h + 8);
-                            st_pm16(scr_d1 + (size_t)l * blk, row, c0, d1);
-                            st_pm16(scr_S + (size_t)l * blk, row, c0, S);
+                            st_pm8(scr_d1 + (size_t)l * blk, row, c0, d1);
+                            st_pm8(scr_S + (size_t)l * blk, row, c0, S);
                         } else {
-                            if (valid) st_bf16x16(a.HbL + (size_t)p * a.wp + c0, h);
-                            float ab[16], hb[16];
+                            if (valid) st_bf16x8(a.HbL + (size_t)p * a.wp + c0, h);
+                            float ab[8], hb[8];
 #pragma unroll
-                            for (int j = 0; j < 16; ++j) {
+                            for (int j = 0; j < 8; ++j) {
                                 hb[j] = alpha_p * wo[c0 + j];
                                 ab[j] = d1[j] * hb[j] + S[j];
                             }
                             st_tile8(tile_h, row, c0, ab);
-                            st_tile8(tile_h, row, c0 + 8, ab + 8);
-                            if (RES) tmem_st_f16(tsec + (uint32_t)c0, hb);
+                            if (RES) tmem_st_f8(tsec + (uint32_t)c0, hb);
                         }
-                    }
-                    if (!ss.after_write()) { ok = false; break; }
+                    };
+                    if (l < L)
+                        chunk_loop<4>(eg, NG, nch,
+                                      [&](int ch, uint32_t (&u)[4]) { ld_pm8_raw(gin, row, ch * 8, u); }, body);
+                    else
+                        chunk_loop<4>(eg, NG, nch, [&](int, uint32_t (&u)[4]) { u[0] = u[1] = u[2] = u[3] = 0; },
+                                      body);
+                    if (!ss.after_write(q < nq - 1 ? aready : nullptr)) { ok = false; break; }
                     if (ss.st_thread) {
                         for (int k = 0; k < nkw; ++k) {
                             tc::tma_store_3d(&a.hdb, tile_d + k * 16384, k * 64, t * 128, l);
@@ -745,44 +816,35 @@ __global__ void __launch_bounds__(kFThreads, 1) k_fused_bwd(const __grid_constan
                     const int l = L - (q - (L + 1));
                     const uint32_t* d1src = scr_d1 + (size_t)(l - 1) * blk;
                     const uint32_t* Ssrc = scr_S + (size_t)(l - 1) * blk;
-                    uint32_t dq[8] = {0, 0, 0, 0, 0, 0, 0, 0}, sq[8] = {0, 0, 0, 0, 0, 0, 0, 0};
-                    if (eg < nch) {
-                        ld_pm16_raw(d1src, row, eg * 16, dq);
-                        ld_pm16_raw(Ssrc, row, eg * 16, sq);
-                    }
-                    for (int ch = eg; ch < nch; ch += 2) {
-                        const int c0 = ch * 16;
-                        float d1[16], S[16];
-                        unpack16(dq, d1);
-                        unpack16(sq, S);
-                        if (ch + 2 < nch) {
-                            ld_pm16_raw(d1src, row, c0 + 32, dq);
-                            ld_pm16_raw(Ssrc, row, c0 + 32, sq);
-                        }
-                        uint32_t rv[16], rr[16];
-                        tc::tmem_ld16(tacc + (uint32_t)c0, rv);
-                        if (RES) tc::tmem_ld16(tsec + (uint32_t)c0, rr);
-                        tc::tmem_wait_ld();
-                        float hb[16], ab[16];
+                    auto ld_adj = [&](int ch, uint32_t (&u)[8]) {
+                            uint32_t* uu = u;
+                            ld_pm8_raw(d1src, row, ch * 8, *reinterpret_cast<uint32_t(*)[4]>(uu));
+                            ld_pm8_raw(Ssrc, row, ch * 8, *reinterpret_cast<uint32_t(*)[4]>(uu + 4));
+                        };
+                    auto body_adj = [&](int ch, const uint32_t (&u)[8]) {
+                            const int c0 = ch * 8;
+                            float d1[8], S[8];
+                            unpack8(*reinterpret_cast<const uint32_t(*)[4]>(u), d1);
+                            unpack8(*reinterpret_cast<const uint32_t(*)[4]>(u + 4), S);
+                            uint32_t rv[8], rr[8];
+                            tc::tmem_ld8(tacc + (uint32_t)c0, rv);
+                            if (RES) tc::tmem_ld8(tsec + (uint32_t)c0, rr);
+                            tc::tmem_wait_ld();
+                            float hb[8], ab[8];
 #pragma unroll
-                        for (int j = 0; j < 16; ++j) {
-                            hb[j] = (RES ? __uint_as_float(rr[j]) : 0.f) + __uint_as_float(rv[j]);
-                            ab[j] = d1[j] * hb[j] + S[j];
-                        }
-                        st_tile8(tile_h, row, c0, ab);
-                        st_tile8(tile_h, row, c0 + 8, ab + 8);
-                        if (RES) tmem_st_f16(tsec + (uint32_t)c0, hb);
-                    }
-                    if (!ss.after_write()) { ok = false; break; }
+                            for (int j = 0; j < 8; ++j) {
+                                hb[j] = (RES ? __uint_as_float(rr[j]) : 0.f) + __uint_as_float(rv[j]);
+                                ab[j] = d1[j] * hb[j] + S[j];
+                            }
+                            st_tile8(tile_h, row, c0, ab);
+                            if (RES) tmem_st_f8(tsec + (uint32_t)c0, hb);
+                        };
+                    chunk_loop<8, decltype(ld_adj), decltype(body_adj), 2>(eg, NG, nch, ld_adj, body_adj);
+                    if (!ss.after_write(q < nq - 1 ? aready : nullptr)) { ok = false; break; }
                     if (ss.st_thread) {
                         for (int k = 0; k < nkw; ++k) tc::tma_store_3d(&a.abb, tile_h + k * 16384, k * 64, t * 128, l - 1);
                         tc::tma_store_commit();
                     }
-                }
-                if (q < nq - 1) {
-                    tc::tmem_wait_st();
-                    tc::tc_fence_before();
-                    tc::mbar_arrive(aready);
                 }
             }
         }
@@ -804,17 +866,18 @@ __global__ void __launch_bounds__(kFThreads, 1) k_fused_bwd(const __grid_constan
 // ---------------------------------------------------------------- host launchers
 
 static size_t fwdz_smem_bytes(int L, int w) {
-    return 1024 + kFTileBytes + (size_t)kFwdStages * kFStageBytes + (size_t)(L + 3) * w * 4 + 512;
+    return 1024 + kFTileBytes + (size_t)kFwdStages * kFStageBytes + (size_t)(L + 3) * w * 4 + 256 +
+           (size_t)kFwdGroups * 128 * 4 + 64;
 }
 static size_t bwd_smem_bytes(int L, int w) {
     return 1024 + 2 * kFTileBytes + (size_t)kBwdStages * kFStageBytes + (size_t)(L + 3) * w * 4 + 512;
 }
 
 template <class K, class A>
-static cudaError_t launch_fused(K kernel, const A& args, int grid, size_t smem, cudaStream_t st) {
+static cudaError_t launch_fused(K kernel, const A& args, int grid, int threads, size_t smem, cudaStream_t st) {
     cudaError_t e = cudaFuncSetAttribute(kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
     if (e != cudaSuccess) return e;
-    kernel<<<grid, kFThreads, smem, st>>>(args);
+    kernel<<<grid, threads, smem, st>>>(args);
     return cudaGetLastError();
 }
 
@@ -845,17 +908,17 @@ fbsde_status fused_forward(fbsde_ctx* c, const float* theta, bool for_grad) {
     a.P = (int)c->P(); a.M = c->M; a.D = c->D; a.Dp = b->Dp; a.Dn = b->Dn; a.w = c->w; a.wp = b->wp;
     a.L = c->L; a.ntiles = (a.P + 127) / 128; a.dt = (float)(c->T / c->N); a.err = b->err;
     const int grid = a.ntiles < b->grid ? a.ntiles : b->grid;
-    FBSDE_CK(c, cudaMemsetAsync(c->Y, 0, (size_t)a.P * sizeof(float), c->stream));
     const size_t smem = fwdz_smem_bytes(c->L, c->w);
+    const int FT = fused_threads(kFwdGroups);
     const bool res = c->akind == FBSDE_RESNET;
     const int tok = prof_begin(c, PROF_POINTS);
     cudaError_t e;
     if (c->act == FBSDE_TANH)
-        e = res ? launch_fused(k_fused_fwdz<FBSDE_TANH, true>, a, grid, smem, c->stream)
-                : launch_fused(k_fused_fwdz<FBSDE_TANH, false>, a, grid, smem, c->stream);
+        e = res ? launch_fused(k_fused_fwdz<FBSDE_TANH, true>, a, grid, FT, smem, c->stream)
+                : launch_fused(k_fused_fwdz<FBSDE_TANH, false>, a, grid, FT, smem, c->stream);
     else
-        e = res ? launch_fused(k_fused_fwdz<FBSDE_SIN, true>, a, grid, smem, c->stream)
-                : launch_fused(k_fused_fwdz<FBSDE_SIN, false>, a, grid, smem, c->stream);
+        e = res ? launch_fused(k_fused_fwdz<FBSDE_SIN, true>, a, grid, FT, smem, c->stream)
+                : launch_fused(k_fused_fwdz<FBSDE_SIN, false>, a, grid, FT, smem, c->stream);
     // algorithmic flops: lift + L layers forward, L reverse layers and the Z contraction
     const double P = a.P, w = a.w, D = a.D;
     prof_end(c, PROF_POINTS, tok, 2.0 * P * w * (2.0 * D + 2.0 * c->L * w));
@@ -883,15 +946,16 @@ fbsde_status fused_backward(fbsde_ctx* c, const float* theta) {
     a.L = c->L; a.ntiles = (a.P + 127) / 128; a.dt = (float)(c->T / c->N); a.err = b->err;
     const int grid = a.ntiles < b->grid ? a.ntiles : b->grid;
     const size_t smem = bwd_smem_bytes(c->L, c->w);
+    const int FT = fused_threads(kBwdGroups);
     const bool res = c->akind == FBSDE_RESNET;
     const int tok = prof_begin(c, PROF_POINTS);
     cudaError_t e;
     if (c->act == FBSDE_TANH)
-        e = res ? launch_fused(k_fused_bwd<FBSDE_TANH, true>, a, grid, smem, c->stream)
-                : launch_fused(k_fused_bwd<FBSDE_TANH, false>, a, grid, smem, c->stream);
+        e = res ? launch_fused(k_fused_bwd<FBSDE_TANH, true>, a, grid, FT, smem, c->stream)
+                : launch_fused(k_fused_bwd<FBSDE_TANH, false>, a, grid, FT, smem, c->stream);
     else
-        e = res ? launch_fused(k_fused_bwd<FBSDE_SIN, true>, a, grid, smem, c->stream)
-                : launch_fused(k_fused_bwd<FBSDE_SIN, false>, a, grid, smem, c->stream);
+        e = res ? launch_fused(k_fused_bwd<FBSDE_SIN, true>, a, grid, FT, smem, c->stream)
+                : launch_fused(k_fused_bwd<FBSDE_SIN, false>, a, grid, FT, smem, c->stream);
     // algorithmic flops: tangent (lift + L layers) and adjoint (L layers); the
     // forward recomputation is overhead and not counted
     const double P = a.P, w = a.w, D = a.D;
