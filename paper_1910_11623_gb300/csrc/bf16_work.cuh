@@ -77,6 +77,7 @@ struct Bf16Work {
     bf16* G = nullptr;     // g_l, l < L, per 128-row tile column-pair-major (written by the fused forward)
     size_t G_stride = 0;   // elements between consecutive g_l
     bf16* scratch = nullptr;  // per-CTA activation-derivative scratch
+    float* pvec = nullptr;    // [(L+3) x w] per-column parameters of the fused backward
 };
 
 

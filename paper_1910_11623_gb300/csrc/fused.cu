@@ -42,20 +42,37 @@ namespace fbsde {
 constexpr uint32_t kFStageBytes = 32768;  // one weight slice: up to 256 rows x 128 B
 constexpr uint32_t kFTileBytes = 65536;   // activation tile: 4 x [128 x 64] BF16
 // Epilogue warp groups (4 warps each, one thread per TMEM lane per group) of
-// the two kernels; each SM sub-partition holds 16K registers, so the forward
-// kernel (3 groups, 14 warps) stays within 128 registers per thread and the
-// backward kernel (2 groups) within 168.
+// the two kernels.  Each SM sub-partition holds 16K registers.  The forward
+// kernel (warps 0-1 producer and MMA, 3 groups: 14 warps) stays within 128
+// registers per thread.  The backward kernel reserves warpgroup 0 (producer,
+// MMA, two idle warps) and runs 2 epilogue warpgroups: launched at 168
+// registers per thread, warpgroup 0 drops to kBwdRegsCtl and the epilogue
+// warpgroups rise to kBwdRegsEpi (setmaxnreg), room for the accumulator
+// columns of the next chunk in flight.
 constexpr int kFwdGroups = 3;
 constexpr int kBwdGroups = 2;
 constexpr int kFDepth = 4;  // chunks of global operands kept in flight per thread
 __host__ __device__ constexpr int fused_threads(int groups) { return 64 + 128 * groups; }
+__host__ __device__ constexpr int bwd_threads() { return 128 + 128 * kBwdGroups; }
+constexpr int kBwdRegsLaunch = (65536 / bwd_threads()) & ~7;
+constexpr uint32_t kBwdRegsCtl = 40, kBwdRegsEpi = 232;
+static_assert(kBwdRegsLaunch == 168, "backward launch register budget");
+static_assert(128 * kBwdRegsCtl + 128 * kBwdGroups * kBwdRegsEpi <= (uint32_t)bwd_threads() * kBwdRegsLaunch,
+              "register split exceeds the launch allocation");
+static_assert(kBwdRegsCtl + kBwdGroups * kBwdRegsEpi <= 512, "register split exceeds an SM sub-partition");
 constexpr int kFwdStages = 4;
 constexpr int kBwdStages = 2;
+// Backward epilogue: chunk iterations per thread that make up one 64-column
+// slab (8 chunks of 8 columns shared by the groups).
+constexpr int kSlabIters = 8 / kBwdGroups;
+static_assert(kSlabIters * kBwdGroups == 8 && kSlabIters % 2 == 0, "slab / group split");
 
 struct FGemm {
     const CUtensorMap* map;
     int nk, K, N, asel;  // K slices, contraction length, output columns, A tile (0 or 1)
     int dual;            // 1: also multiply tile 1 by the same weights into TMEM columns 256..
+    int dcol = 0;        // TMEM column of the accumulator
+    int acc = 0;         // 1: add to the accumulator's contents (a residual kept there)
 };
 
 // ---------------------------------------------------------------- small helpers
@@ -118,6 +135,13 @@ __device__ __forceinline__ void tmem_st_f8(uint32_t taddr, const float* v) {
     for (int j = 0; j < 8; ++j) u[j] = __float_as_uint(v[j]);
     tc::tmem_st8(taddr, u);
 }
+// Eight consecutive floats from a 16-byte-aligned address.
+__device__ __forceinline__ void ld_f8(const float* src, float* v) {
+    const float4 a = reinterpret_cast<const float4*>(src)[0];
+    const float4 b = reinterpret_cast<const float4*>(src)[1];
+    v[0] = a.x; v[1] = a.y; v[2] = a.z; v[3] = a.w;
+    v[4] = b.x; v[5] = b.y; v[6] = b.z; v[7] = b.w;
+}
 __device__ __forceinline__ void st_bf16x8(bf16* dst, const float* v) {
     uint4 u;
     u.x = pack_bf16x2(v[0], v[1]); u.y = pack_bf16x2(v[2], v[3]);
@@ -142,6 +166,17 @@ __device__ __forceinline__ void st_pm8(uint32_t* blk, int row, int c0, const flo
     uint32_t* q = blk + (c0 >> 1) * 128 + row;
 #pragma unroll
     for (int k = 0; k < 4; ++k) q[k * 128] = pack_bf16x2(v[2 * k], v[2 * k + 1]);
+}
+// Cache-hinted variants (L2 eviction policy `pol`).
+__device__ __forceinline__ void st_pm8h(uint32_t* blk, int row, int c0, const float* v, uint64_t pol) {
+    uint32_t* q = blk + (c0 >> 1) * 128 + row;
+#pragma unroll
+    for (int k = 0; k < 4; ++k) tc::st_global_hint(q + k * 128, pack_bf16x2(v[2 * k], v[2 * k + 1]), pol);
+}
+__device__ __forceinline__ void ld_pm8h(const uint32_t* blk, int row, int c0, uint32_t (&u)[4], uint64_t pol) {
+    const uint32_t* q = blk + (c0 >> 1) * 128 + row;
+#pragma unroll
+    for (int k = 0; k < 4; ++k) u[k] = tc::ld_global_hint(q + k * 128, pol);
 }
 __device__ __forceinline__ void ld_pm8_raw(const uint32_t* blk, int row, int c0, uint32_t (&u)[4]) {
     const uint32_t* q = blk + (c0 >> 1) * 128 + row;
@@ -188,23 +223,70 @@ __device__ __forceinline__ void chunk_loop(int first, int step, int n, Load load
     }
 }
 
+// chunk_loop with the accumulator columns of each chunk read from TMEM one
+// chunk ahead: loadt(ch, regs) issues the (up to two 8-column) TMEM loads of
+// chunk ch, and the wait for them comes only when chunk ch is next, so the
+// TMEM latency overlaps the body of the chunk before.  DEPTH must be even.
+// The chunks come in `nblocks` blocks of DEPTH per thread (the same count in
+// every thread, whatever its share of the n chunks); block(b) runs after
+// block b.
+template <int NW, int DEPTH, class LoadG, class LoadT, class Body, class Block>
+__device__ __forceinline__ void chunk_loop_t(int first, int step, int n, int nblocks, LoadG loadg, LoadT loadt,
+                                             Body body, Block block) {
+    static_assert(DEPTH % 2 == 0, "TMEM double buffer indexing needs an even depth");
+    uint32_t gb[DEPTH][NW];
+    uint32_t tb[2][16];
+#pragma unroll
+    for (int d = 0; d < DEPTH; ++d)
+        if (first + d * step < n) loadg(first + d * step, gb[d]);
+    if (first < n) loadt(first, tb[0]);
+    for (int b = 0; b < nblocks; ++b) {
+        const int base = b * DEPTH;
+#pragma unroll
+        for (int d = 0; d < DEPTH; ++d) {
+            const int ch = first + (base + d) * step;
+            if (ch < n) {
+                tc::tmem_wait_ld_regs(tb[d & 1]);
+                uint32_t cg[NW], ct[16];
+#pragma unroll
+                for (int k = 0; k < NW; ++k) cg[k] = gb[d][k];
+#pragma unroll
+                for (int k = 0; k < 16; ++k) ct[k] = tb[d & 1][k];
+                if (ch + step < n) loadt(ch + step, tb[(d + 1) & 1]);
+                if (ch + DEPTH * step < n) loadg(ch + DEPTH * step, gb[d]);
+                body(ch, cg, ct);
+            }
+        }
+        block(b);
+    }
+}
+
 // Tiles leave shared memory by TMA bulk stores issued by one epilogue thread.
-// Every phase that writes tiles is bracketed: before writing, the storing
-// thread waits until earlier stores have read their tiles and opens `tfree`;
-// after writing, every epilogue thread fences its writes for the async proxy
-// and arrives on `wdone`, which the storing thread waits for before it issues
-// the stores of this phase.  Both waits are bounded.
+// Before a phase writes tiles, the storing thread waits until earlier stores
+// have read them and opens `tfree` (bounded wait for all).  The forward
+// kernel stores after a phase: every epilogue thread fences its writes for
+// the async proxy and arrives on `wdone`, which the storing thread waits for
+// (bounded) before it issues the stores.  The backward kernel stores each
+// 64-column slab as soon as a named barrier says all its chunks are written,
+// and hands the tiles to the MMA issuer with handoff().
 struct StoreSync {
     uint64_t* tfree;  // count 1: the storing thread
     uint64_t* wdone;  // count: every epilogue thread
     bool st_thread;
-    uint32_t phase;
+    uint32_t tphase, wphase;
     __device__ bool before_write() {
         if (st_thread) {
             tc::tma_store_wait_read<0>();
             tc::mbar_arrive(tfree);
         }
-        return tc::mbar_wait(tfree, phase & 1u, tc::kWaitBudget);
+        return tc::mbar_wait(tfree, (tphase++) & 1u, tc::kWaitBudget);
+    }
+    // every epilogue thread: the tiles written (and fenced for the async
+    // proxy) go to the MMA issuer; no stores wait on this
+    __device__ void handoff(uint64_t* aready) {
+        tc::tmem_wait_st();
+        tc::tc_fence_before();
+        tc::mbar_arrive(aready);
     }
     // returns false on timeout; the storing thread may issue stores after it.
     // With `aready`, every thread also hands the tiles to the MMA issuer
@@ -219,8 +301,8 @@ struct StoreSync {
             tc::mbar_arrive(aready);
         }
         bool ok = true;
-        if (st_thread) ok = tc::mbar_wait(wdone, phase & 1u, tc::kWaitBudget);
-        ++phase;
+        if (st_thread) ok = tc::mbar_wait(wdone, wphase & 1u, tc::kWaitBudget);
+        ++wphase;
         return ok;
     }
 };
@@ -307,7 +389,7 @@ __device__ void mma_role(const Sched& sch, int ntiles, int nstages, uint32_t aba
                 for (int k = 0; k < nsteps; ++k) {
                     const uint64_t ad = tc::sdesc_sw128(abase + (uint32_t)kc * 16384u + 32u * k, 16u);
                     const uint64_t bd = tc::sdesc_sw128(rbase + (uint32_t)s * kFStageBytes + 32u * k, 16u);
-                    tc::mma_bf16(tmem, ad, bd, idesc, (kc > 0 || k > 0) ? 1u : 0u);
+                    tc::mma_bf16(tmem + (uint32_t)g.dcol, ad, bd, idesc, (g.acc || kc > 0 || k > 0) ? 1u : 0u);
                     if (dual) {
                         const uint64_t ad1 = tc::sdesc_sw128(abase1 + (uint32_t)kc * 16384u + 32u * k, 16u);
                         tc::mma_bf16(tmem + 256u, ad1, bd, idesc, (kc > 0 || k > 0) ? 1u : 0u);
@@ -435,7 +517,10 @@ __global__ void __launch_bounds__(fused_threads(kFwdGroups), 1) k_fused_fwdz(con
         const float* win0 = ptab + (L + 2) * a.w;
         const size_t blk = (size_t)(a.w / 2) * 128;  // words of one column-pair-major 128-row block
         uint32_t* scr = a.scratch + (size_t)blockIdx.x * L * blk;
-        StoreSync ss{tfree, wdone, warp == 2 && lane == 0, 0u};
+        StoreSync ss{tfree, wdone, warp == 2 && lane == 0, 0u, 0u};
+        // L2 policies: per-CTA scratch stays (re-read within microseconds),
+        // the g_l / e_l streams go out first (read by later kernels)
+        const uint64_t pol_keep = tc::l2_policy_evict_last(), pol_stream = tc::l2_policy_evict_first();
         const int nq = sch.nq();
         const int nkw = a.wp / 64;
         const int nch = a.w / 8;
@@ -487,7 +572,7 @@ __global__ void __launch_bounds__(fused_threads(kFwdGroups), 1) k_fused_fwdz(con
                         }
                         if (l < L) {
                             st_tile8(tile, row, c0, h);
-                            st_pm8(sc, row, c0, d1);
+                            st_pm8h(sc, row, c0, d1, pol_keep);
                             if (RES) tmem_st_f8(tres + (uint32_t)c0, h);
                         } else {
                             // top: y = w_o^T h_L + b_o and e_L = act'(a_L) w_o
@@ -534,7 +619,7 @@ __global__ void __launch_bounds__(fused_threads(kFwdGroups), 1) k_fused_fwdz(con
                                 g[j] = gl + __uint_as_float(rv[j]);
                                 e[j] = d1[j] * g[j];
                             }
-                            if (a.for_grad) st_pm8(gout, row, c0, g);
+                            if (a.for_grad) st_pm8h(gout, row, c0, g, pol_stream);
                             st_tile8(tile, row, c0, e);
                             if (RES) tmem_st_f8(tres + (uint32_t)c0, g);
                         });
@@ -556,7 +641,8 @@ __global__ void __launch_bounds__(fused_threads(kFwdGroups), 1) k_fused_fwdz(con
                 if (writes_tile) {
                     if (!ss.after_write(q < nq - 1 ? aready : nullptr)) { ok = false; break; }
                     if (ss.st_thread && a.for_grad && store_layer >= 0) {
-                        for (int k = 0; k < nkw; ++k) tc::tma_store_3d(&a.eb, tile + k * 16384, k * 64, t * 128, store_layer);
+                        for (int k = 0; k < nkw; ++k)
+                            tc::tma_store_3d_hint(&a.eb, tile + k * 16384, k * 64, t * 128, store_layer, pol_stream);
                         tc::tma_store_commit();
                     }
                 } else if (q < nq - 1) {
@@ -597,7 +683,9 @@ struct BwdArgs {
     bf16* HbL;                 // h_L rows of wp (its tile slot holds abar_L)
     uint32_t* scratch;         // per CTA: act'(a_l) and S_l, l < L, column-pair-major
     ParamOffsets off;
+    const float* pvec;  // [(L+3) x w]: b_0..b_L, w_o, W_in[:,0]
     int P, M, D, Dp, w, wp, L, ntiles;
+    int res;            // ResNet: hbar accumulates in place in TMEM columns 256..
     float dt;
     int* err;
 };
@@ -621,6 +709,8 @@ struct BwdSched {
             const int l = L - (q - (L + 1));
             g.asel = 0;
             g.dual = 0;
+            g.dcol = a->res ? 256 : 0;
+            g.acc = a->res;
             g.map = &a->wr[l];
             g.nk = a->wp / 64;
             g.K = a->w;
@@ -647,7 +737,7 @@ struct BwdSched {
 // FP32 residual of k_fused_fwdz has no room here: TMEM holds both the forward
 // and the tangent accumulators), and carries the tangent h' in BF16 as well.
 template <int ACT, bool RES>
-__global__ void __launch_bounds__(fused_threads(kBwdGroups), 1) k_fused_bwd(const __grid_constant__ BwdArgs a) {
+__global__ void __launch_bounds__(bwd_threads(), 1) k_fused_bwd(const __grid_constant__ BwdArgs a) {
     constexpr int NG = kBwdGroups, NE = 128 * NG;
     extern __shared__ uint8_t smem_raw[];
     uint8_t* smem = (uint8_t*)(((uintptr_t)smem_raw + 1023) & ~(uintptr_t)1023);
@@ -669,7 +759,8 @@ __global__ void __launch_bounds__(fused_threads(kBwdGroups), 1) k_fused_bwd(cons
     const int L = a.L;
     const BwdSched sch{&a};
 
-    stage_params(ptab, a.theta, a.off, L, a.w, a.D + 1);
+    for (int k = threadIdx.x; k < (L + 3) * a.w / 4; k += blockDim.x)
+        reinterpret_cast<float4*>(ptab)[k] = __ldg(reinterpret_cast<const float4*>(a.pvec) + k);
     if (threadIdx.x == 0) {
         for (int s = 0; s < kBwdStages; ++s) {
             tc::mbar_init(&bfull[s], 1);
@@ -692,29 +783,43 @@ __global__ void __launch_bounds__(fused_threads(kBwdGroups), 1) k_fused_bwd(cons
     tc::tc_fence_after();
     const uint32_t tmem = *tslot;
 
-    if (warp == 0) {
-        if (lane == 0) producer_role(sch, a.ntiles, kBwdStages, ring, bfull, bempty, abort_flag, a.err);
-    } else if (warp == 1) {
-        if (lane == 0)
-            mma_role(sch, a.ntiles, kBwdStages, tc::smem_u32(tile_h), tc::smem_u32(tile_d), tc::smem_u32(ring),
-                     tmem, bfull, bempty, accf, aready, abort_flag, a.err);
+    if (warp < 4) {
+        tc::setmaxnreg_dec<kBwdRegsCtl>();
+        if (warp == 0) {
+            if (lane == 0) producer_role(sch, a.ntiles, kBwdStages, ring, bfull, bempty, abort_flag, a.err);
+        } else if (warp == 1) {
+            if (lane == 0)
+                mma_role(sch, a.ntiles, kBwdStages, tc::smem_u32(tile_h), tc::smem_u32(tile_d), tc::smem_u32(ring),
+                         tmem, bfull, bempty, accf, aready, abort_flag, a.err);
+        }
     } else {
-        const int eg = (warp - 2) >> 2;
+        tc::setmaxnreg_inc<kBwdRegsEpi>();
+        const int eg = (warp - 4) >> 2;
         const int lg = warp & 3;
         const int row = lg * 32 + lane;
         const uint32_t tacc = tmem + ((uint32_t)(lg * 32) << 16);
         const uint32_t tsec = tacc + 256u;  // tangent accumulator in the up-sweep, hbar in the down-sweep
-        const float* wo = ptab + (L + 1) * a.w;
-        const float* win0 = ptab + (L + 2) * a.w;
+        // per-column parameters (biases, w_o, W_in[:,0]): 16-byte broadcast
+        // loads from a small table in global memory; the shared memory holds
+        // a third weight stage instead
+        const float* wo = ptab + (size_t)(L + 1) * a.w;
+        const float* win0 = ptab + (size_t)(L + 2) * a.w;
         const size_t blk = (size_t)(a.w / 2) * 128;
         uint32_t* scr_d1 = a.scratch + (size_t)blockIdx.x * 2 * L * blk;  // act'(a_l), l < L
         uint32_t* scr_S = scr_d1 + (size_t)L * blk;                       // S_l, l < L
-        StoreSync ss{tfree, wdone, warp == 2 && lane == 0, 0u};
+        StoreSync ss{tfree, wdone, warp == 4 && lane == 0, 0u, 0u};
+        // L2 policies: per-CTA scratch stays (re-read within microseconds),
+        // g_l and the operand stacks stream
+        const uint64_t pol_keep = tc::l2_policy_evict_last(), pol_stream = tc::l2_policy_evict_first();
         const int nq = sch.nq();
         const int nch = a.w / 8;
         const int nkw = a.wp / 64, nkx = a.Dp / 64;
         int qg = 0, tcount = 0;
         bool ok = true;
+        // A wait that runs out of budget clears `ok` but the thread still
+        // goes through the phase (the named barriers of the slab stores need
+        // every epilogue thread); at the end of each phase all of them take
+        // the same decision, so none is left waiting at a barrier.
         for (int t = blockIdx.x; t < a.ntiles && ok; t += gridDim.x) {
             const int p = t * 128 + row;
             const bool valid = p < a.P;
@@ -722,7 +827,7 @@ __global__ void __launch_bounds__(fused_threads(kBwdGroups), 1) k_fused_bwd(cons
             const float alpha_p = valid ? __ldg(a.alpha + p) : 0.f;
             const uint32_t* gtile = a.G + (size_t)t * blk;
             // inputs: (t, X) for the forward, (0, v) for the tangent, BF16 rows by TMA
-            if (!ss.before_write()) { ok = false; break; }
+            if (ok) ok = ss.before_write();
             if (ss.st_thread) {
                 tc::mbar_expect_tx(xfull, (uint32_t)nkx * 2u * 16384u);
                 for (int k = 0; k < nkx; ++k) {
@@ -730,49 +835,47 @@ __global__ void __launch_bounds__(fused_threads(kBwdGroups), 1) k_fused_bwd(cons
                     tc::tma_load_2d(tile_d + k * 16384, &a.vb, xfull, k * 64, t * 128);
                 }
             }
-            if (!tc::mbar_wait(xfull, (uint32_t)tcount & 1u, tc::kWaitBudget)) { ok = false; break; }
+            if (ok) ok = tc::mbar_wait(xfull, (uint32_t)tcount & 1u, tc::kWaitBudget);
             ++tcount;
-            if (!ss.after_write(aready)) { ok = false; break; }
+            if (ok) ok = ss.after_write(aready);
             for (int q = 0; q < nq; ++q, ++qg) {
-                if (!tc::mbar_wait(accf, (uint32_t)qg & 1u, tc::kWaitBudget)) {
-                    ok = false;
-                    break;
-                }
+                if (ok) ok = tc::mbar_wait(accf, (uint32_t)qg & 1u, tc::kWaitBudget);
                 tc::tc_fence_after();
-                if (!ss.before_write()) { ok = false; break; }
+                if (ok) ok = ss.before_write();
                 if (q <= L) {
                     // layer l forward and tangent:
                     //   a = acc + b (+ t W_in[:,0]),  h_l = [h_{l-1}] + act(a)
                     //   h'_l = [h'_{l-1}] + act'(a) a',  S_l = act''(a) a' g_l
                     // at the top (l = L) also abar_L = act'(a_L) alpha w_o + S_L and hbar_L = alpha w_o
                     const int l = q;
-                    const float* bias = ptab + l * a.w;
+                    const float* bias = ptab + (size_t)l * a.w;
                     const uint32_t* gin = gtile + (size_t)l * a.G_words;
-                    auto body = [&](int ch, const uint32_t (&gq)[4]) {
+                    auto loadt = [&](int ch, uint32_t (&r)[16]) {
+                        tc::tmem_ld8(tacc + (uint32_t)(ch * 8), *reinterpret_cast<uint32_t(*)[8]>(r));
+                        tc::tmem_ld8(tsec + (uint32_t)(ch * 8), *reinterpret_cast<uint32_t(*)[8]>(r + 8));
+                    };
+                    auto body = [&](int ch, const uint32_t (&gq)[4], const uint32_t (&rt)[16]) {
                         const int c0 = ch * 8;
-                        float g[8];
-                        if (l < L) {
-                            unpack8(gq, g);
-                        } else {
-#pragma unroll
-                            for (int j = 0; j < 8; ++j) g[j] = wo[c0 + j];
-                        }
-                        uint32_t rf[8], rt[8];
-                        tc::tmem_ld8(tacc + (uint32_t)c0, rf);
-                        tc::tmem_ld8(tsec + (uint32_t)c0, rt);
-                        float hp[8], hdp[8];
+                        float g[8], bv[8], hp[8], hdp[8];
+                        ld_f8(bias + c0, bv);
+                        if (l < L) unpack8(gq, g);
+                        else ld_f8(wo + c0, g);
                         if (RES && l >= 1) {
                             ld_tile8(tile_h, row, c0, hp);
                             ld_tile8(tile_d, row, c0, hdp);
                         }
-                        tc::tmem_wait_ld();
+                        if (l == 0) {
+                            float w0[8];
+                            ld_f8(win0 + c0, w0);
+#pragma unroll
+                            for (int j = 0; j < 8; ++j) bv[j] = fmaf(tval, w0[j], bv[j]);
+                        }
                         float h[8], hd[8], d1[8], S[8];
 #pragma unroll
                         for (int j = 0; j < 8; ++j) {
-                            float av = __uint_as_float(rf[j]) + bias[c0 + j];
-                            if (l == 0) av = fmaf(tval, win0[c0 + j], av);
+                            const float av = __uint_as_float(rt[j]) + bv[j];
                             const Act3 f = act3_sfu<ACT>(av);
-                            const float ad = __uint_as_float(rt[j]);
+                            const float ad = __uint_as_float(rt[8 + j]);
                             h[j] = ((RES && l >= 1) ? hp[j] : 0.f) + f.f;
                             hd[j] = ((RES && l >= 1) ? hdp[j] : 0.f) + f.d1 * ad;
                             S[j] = f.d2 * ad * g[j];
@@ -781,35 +884,41 @@ __global__ void __launch_bounds__(fused_threads(kBwdGroups), 1) k_fused_bwd(cons
                         st_tile8(tile_d, row, c0, hd);
                         if (l < L) {
                             st_tile8(tile_h, row, c0, h);
-                            st_pm8(scr_d1 + (size_t)l * blk, row, c0, d1);
-                            st_pm8(scr_S + (size_t)l * blk, row, c0, S);
+                            st_pm8h(scr_d1 + (size_t)l * blk, row, c0, d1, pol_keep);
+                            st_pm8h(scr_S + (size_t)l * blk, row, c0, S, pol_keep);
                         } else {
                             if (valid) st_bf16x8(a.HbL + (size_t)p * a.wp + c0, h);
                             float ab[8], hb[8];
 #pragma unroll
                             for (int j = 0; j < 8; ++j) {
-                                hb[j] = alpha_p * wo[c0 + j];
+                                hb[j] = alpha_p * g[j];  // g = w_o at the top
                                 ab[j] = d1[j] * hb[j] + S[j];
                             }
                             st_tile8(tile_h, row, c0, ab);
                             if (RES) tmem_st_f8(tsec + (uint32_t)c0, hb);
                         }
                     };
-                    if (l < L)
-                        chunk_loop<4>(eg, NG, nch,
-                                      [&](int ch, uint32_t (&u)[4]) { ld_pm8_raw(gin, row, ch * 8, u); }, body);
-                    else
-                        chunk_loop<4>(eg, NG, nch, [&](int, uint32_t (&u)[4]) { u[0] = u[1] = u[2] = u[3] = 0; },
-                                      body);
-                    if (!ss.after_write(q < nq - 1 ? aready : nullptr)) { ok = false; break; }
-                    if (ss.st_thread) {
-                        for (int k = 0; k < nkw; ++k) {
-                            tc::tma_store_3d(&a.hdb, tile_d + k * 16384, k * 64, t * 128, l);
-                            if (l < L) tc::tma_store_3d(&a.hb, tile_h + k * 16384, k * 64, t * 128, l);
-                            else tc::tma_store_3d(&a.abb, tile_h + k * 16384, k * 64, t * 128, L);
+                    // each finished 64-column slab leaves by TMA while the
+                    // epilogue goes on with the next one
+                    auto slab = [&](int k) {
+                        tc::fence_async_shared();
+                        tc::named_bar(1, NE);
+                        if (ss.st_thread) {
+                            tc::tma_store_3d_hint(&a.hdb, tile_d + k * 16384, k * 64, t * 128, l, pol_stream);
+                            if (l < L) tc::tma_store_3d_hint(&a.hb, tile_h + k * 16384, k * 64, t * 128, l, pol_stream);
+                            else tc::tma_store_3d_hint(&a.abb, tile_h + k * 16384, k * 64, t * 128, L, pol_stream);
+                            tc::tma_store_commit();
                         }
-                        tc::tma_store_commit();
-                    }
+                    };
+                    if (l < L)
+                        chunk_loop_t<4, kSlabIters>(eg, NG, nch, nkw,
+                                                    [&](int ch, uint32_t (&u)[4]) { ld_pm8h(gin, row, ch * 8, u, pol_stream); },
+                                                    loadt, body, slab);
+                    else
+                        chunk_loop_t<4, kSlabIters>(eg, NG, nch, nkw,
+                                                    [&](int, uint32_t (&u)[4]) { u[0] = u[1] = u[2] = u[3] = 0; },
+                                                    loadt, body, slab);
+                    if (q < nq - 1) ss.handoff(aready);
                 } else {
                     // adjoint through layer l: hbar_{l-1} = [hbar_l] + W_l^T abar_l,
                     // abar_{l-1} = act'(a_{l-1}) hbar_{l-1} + S_{l-1}
@@ -817,35 +926,38 @@ __global__ void __launch_bounds__(fused_threads(kBwdGroups), 1) k_fused_bwd(cons
                     const uint32_t* d1src = scr_d1 + (size_t)(l - 1) * blk;
                     const uint32_t* Ssrc = scr_S + (size_t)(l - 1) * blk;
                     auto ld_adj = [&](int ch, uint32_t (&u)[8]) {
-                            uint32_t* uu = u;
-                            ld_pm8_raw(d1src, row, ch * 8, *reinterpret_cast<uint32_t(*)[4]>(uu));
-                            ld_pm8_raw(Ssrc, row, ch * 8, *reinterpret_cast<uint32_t(*)[4]>(uu + 4));
-                        };
-                    auto body_adj = [&](int ch, const uint32_t (&u)[8]) {
-                            const int c0 = ch * 8;
-                            float d1[8], S[8];
-                            unpack8(*reinterpret_cast<const uint32_t(*)[4]>(u), d1);
-                            unpack8(*reinterpret_cast<const uint32_t(*)[4]>(u + 4), S);
-                            uint32_t rv[8], rr[8];
-                            tc::tmem_ld8(tacc + (uint32_t)c0, rv);
-                            if (RES) tc::tmem_ld8(tsec + (uint32_t)c0, rr);
-                            tc::tmem_wait_ld();
-                            float hb[8], ab[8];
+                        uint32_t* uu = u;
+                        ld_pm8_raw(d1src, row, ch * 8, *reinterpret_cast<uint32_t(*)[4]>(uu));
+                        ld_pm8_raw(Ssrc, row, ch * 8, *reinterpret_cast<uint32_t(*)[4]>(uu + 4));
+                    };
+                    // ResNet: the contraction added W_l^T abar_l to hbar_l in
+                    // place (columns 256..), so the accumulator is hbar_{l-1}
+                    const uint32_t thb = RES ? tsec : tacc;
+                    auto ldt_adj = [&](int ch, uint32_t (&r)[16]) {
+                        tc::tmem_ld8(thb + (uint32_t)(ch * 8), *reinterpret_cast<uint32_t(*)[8]>(r));
+                    };
+                    auto body_adj = [&](int ch, const uint32_t (&u)[8], const uint32_t (&rt)[16]) {
+                        const int c0 = ch * 8;
+                        float d1[8], S[8], ab[8];
+                        unpack8(*reinterpret_cast<const uint32_t(*)[4]>(u), d1);
+                        unpack8(*reinterpret_cast<const uint32_t(*)[4]>(u + 4), S);
 #pragma unroll
-                            for (int j = 0; j < 8; ++j) {
-                                hb[j] = (RES ? __uint_as_float(rr[j]) : 0.f) + __uint_as_float(rv[j]);
-                                ab[j] = d1[j] * hb[j] + S[j];
-                            }
-                            st_tile8(tile_h, row, c0, ab);
-                            if (RES) tmem_st_f8(tsec + (uint32_t)c0, hb);
-                        };
-                    chunk_loop<8, decltype(ld_adj), decltype(body_adj), 2>(eg, NG, nch, ld_adj, body_adj);
-                    if (!ss.after_write(q < nq - 1 ? aready : nullptr)) { ok = false; break; }
-                    if (ss.st_thread) {
-                        for (int k = 0; k < nkw; ++k) tc::tma_store_3d(&a.abb, tile_h + k * 16384, k * 64, t * 128, l - 1);
-                        tc::tma_store_commit();
-                    }
+                        for (int j = 0; j < 8; ++j) ab[j] = d1[j] * __uint_as_float(rt[j]) + S[j];
+                        st_tile8(tile_h, row, c0, ab);
+                    };
+                    auto slab = [&](int k) {
+                        tc::fence_async_shared();
+                        tc::named_bar(1, NE);
+                        if (ss.st_thread) {
+                            tc::tma_store_3d_hint(&a.abb, tile_h + k * 16384, k * 64, t * 128, l - 1, pol_stream);
+                            tc::tma_store_commit();
+                        }
+                    };
+                    chunk_loop_t<8, kSlabIters>(eg, NG, nch, nkw, ld_adj, ldt_adj, body_adj, slab);
+                    if (q < nq - 1) ss.handoff(aready);
                 }
+                ok = tc::named_bar_and(1, NE, ok);
+                if (!ok) break;
             }
         }
         if (ss.st_thread) tc::tma_store_wait_all<0>();
@@ -870,13 +982,23 @@ static size_t fwdz_smem_bytes(int L, int w) {
            (size_t)kFwdGroups * 128 * 4 + 64;
 }
 static size_t bwd_smem_bytes(int L, int w) {
-    return 1024 + 2 * kFTileBytes + (size_t)kBwdStages * kFStageBytes + (size_t)(L + 3) * w * 4 + 512;
+    return 1024 + 2 * kFTileBytes + (size_t)kBwdStages * kFStageBytes + (size_t)(L + 3) * w * 4 + 128;
 }
 
+// `launch_regs` > 0: the kernel moves registers between warpgroups, which
+// needs exactly that many registers per thread at launch; any other count is
+// refused here rather than launched.
 template <class K, class A>
-static cudaError_t launch_fused(K kernel, const A& args, int grid, int threads, size_t smem, cudaStream_t st) {
+static cudaError_t launch_fused(K kernel, const A& args, int grid, int threads, size_t smem, cudaStream_t st,
+                                int launch_regs = 0) {
     cudaError_t e = cudaFuncSetAttribute(kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
     if (e != cudaSuccess) return e;
+    if (launch_regs > 0) {
+        cudaFuncAttributes fa;
+        e = cudaFuncGetAttributes(&fa, kernel);
+        if (e != cudaSuccess) return e;
+        if (fa.numRegs != launch_regs || fa.maxThreadsPerBlock < threads) return cudaErrorInvalidConfiguration;
+    }
     kernel<<<grid, threads, smem, st>>>(args);
     return cudaGetLastError();
 }
@@ -927,6 +1049,21 @@ fbsde_status fused_forward(fbsde_ctx* c, const float* theta, bool for_grad) {
     return FBSDE_OK;
 }
 
+// Per-column parameters of the backward (b_0..b_L, w_o, W_in[:,0]) gathered
+// into one aligned table.
+__global__ void k_stage_pvec(const float* __restrict__ th, ParamOffsets o, int L, int w, int K0,
+                             float* __restrict__ pvec) {
+    const int n = (L + 3) * w;
+    for (int i = blockIdx.x * blockDim.x + threadIdx.x; i < n; i += gridDim.x * blockDim.x) {
+        const int l = i / w, c = i % w;
+        float v;
+        if (l <= L) v = th[(l == 0 ? o.bin : o.b[l]) + c];
+        else if (l == L + 1) v = th[o.wo + c];
+        else v = th[o.Win + (size_t)c * K0];
+        pvec[i] = v;
+    }
+}
+
 fbsde_status fused_backward(fbsde_ctx* c, const float* theta) {
     Bf16Work* b = c->bf;
     BwdArgs a;
@@ -944,18 +1081,26 @@ fbsde_status fused_backward(fbsde_ctx* c, const float* theta) {
     a.off = param_offsets(c);
     a.P = (int)c->P(); a.M = c->M; a.D = c->D; a.Dp = b->Dp; a.w = c->w; a.wp = b->wp;
     a.L = c->L; a.ntiles = (a.P + 127) / 128; a.dt = (float)(c->T / c->N); a.err = b->err;
+    a.pvec = b->pvec;
+    a.res = c->akind == FBSDE_RESNET ? 1 : 0;
+    k_stage_pvec<<<4, 256, 0, c->stream>>>(theta, a.off, c->L, c->w, c->D + 1, b->pvec);
+    {
+        cudaError_t le = cudaGetLastError();
+        if (le != cudaSuccess) return set_err(c, FBSDE_ERR_CUDA, std::string("parameter table: ") + cudaGetErrorString(le));
+        ++c->n_launch;
+    }
     const int grid = a.ntiles < b->grid ? a.ntiles : b->grid;
     const size_t smem = bwd_smem_bytes(c->L, c->w);
-    const int FT = fused_threads(kBwdGroups);
+    const int FT = bwd_threads(), R = kBwdRegsLaunch;
     const bool res = c->akind == FBSDE_RESNET;
     const int tok = prof_begin(c, PROF_POINTS);
     cudaError_t e;
     if (c->act == FBSDE_TANH)
-        e = res ? launch_fused(k_fused_bwd<FBSDE_TANH, true>, a, grid, FT, smem, c->stream)
-                : launch_fused(k_fused_bwd<FBSDE_TANH, false>, a, grid, FT, smem, c->stream);
+        e = res ? launch_fused(k_fused_bwd<FBSDE_TANH, true>, a, grid, FT, smem, c->stream, R)
+                : launch_fused(k_fused_bwd<FBSDE_TANH, false>, a, grid, FT, smem, c->stream, R);
     else
-        e = res ? launch_fused(k_fused_bwd<FBSDE_SIN, true>, a, grid, FT, smem, c->stream)
-                : launch_fused(k_fused_bwd<FBSDE_SIN, false>, a, grid, FT, smem, c->stream);
+        e = res ? launch_fused(k_fused_bwd<FBSDE_SIN, true>, a, grid, FT, smem, c->stream, R)
+                : launch_fused(k_fused_bwd<FBSDE_SIN, false>, a, grid, FT, smem, c->stream, R);
     // algorithmic flops: tangent (lift + L layers) and adjoint (L layers); the
     // forward recomputation is overhead and not counted
     const double P = a.P, w = a.w, D = a.D;

@@ -109,6 +109,7 @@ fbsde_status bf16_create(fbsde_ctx* c) {
     if (b->fused) {
         add((size_t)(L > 0 ? L : 1) * b->G_stride * sizeof(bf16));
         add((size_t)b->grid * (2 * L + 2) * 128 * w * sizeof(bf16));
+        add((size_t)(L + 3) * w * sizeof(float));
     }
     cudaError_t e = cudaMalloc(&b->mem, bytes);
     if (e != cudaSuccess) {
@@ -147,6 +148,7 @@ fbsde_status bf16_create(fbsde_ctx* c) {
     if (b->fused) {
         b->G = (bf16*)take((size_t)(L > 0 ? L : 1) * b->G_stride * sizeof(bf16));
         b->scratch = (bf16*)take((size_t)b->grid * (2 * L + 2) * 128 * w * sizeof(bf16));
+        b->pvec = (float*)take((size_t)(L + 3) * w * sizeof(float));
     }
 
     bool ok = true;
