@@ -203,6 +203,43 @@ def time_steps(solver, theta, m, v, first_step, K, lr):
     return e0.elapsed_time(e1)
 
 
+def multilevel_run(P, w, target, max_steps):
+    """Multilevel training (Section 3.2) from the same Theta_0 as the
+    single-level accuracy run: fixed Adam steps on the coarse grids, then the
+    target grid until |Y0 - closed form| <= 1% (checked every 50 steps, as in
+    the single-level run).  Wall time includes every level."""
+    import torch
+    levels = list(P.workloads.MULTILEVEL_LEVELS)
+    N = w.problem.N
+    s = P.Solver(w.problem, w.arch, seed=w.seed, N_max=N)
+    th = s.init_params()
+    m, v = torch.zeros_like(th), torch.zeros_like(th)
+    torch.cuda.synchronize()
+    t0 = time.perf_counter()
+    step, hit, per_level = 1, None, []
+    for lv in levels:
+        budget = P.workloads.MULTILEVEL_COARSE_STEPS if lv < N else max_steps
+        done = 0
+        tl = time.perf_counter()
+        while done < budget:
+            k = min(50, budget - done)
+            _, y0 = s.train_schedule(th, m, v, [lv], [k], step, w.lr)
+            step += k
+            done += k
+            err = abs(y0[-1].item() - target) / target
+            if lv == N and err <= 0.01:
+                hit = (time.perf_counter() - t0, step - 1)
+                break
+        per_level.append({"N": lv, "steps": done, "wall_s": time.perf_counter() - tl, "y0_rel_err": err})
+        if hit:
+            break
+    res = {"levels": levels, "coarse_steps_per_level": P.workloads.MULTILEVEL_COARSE_STEPS,
+           "per_level": per_level, "time_to_1pct_s": hit[0] if hit else None,
+           "steps_to_1pct": hit[1] if hit else None, "wall_s": time.perf_counter() - t0}
+    s.close()
+    return res
+
+
 def main():
     args = parse_args()
     world = int(os.environ.get("WORLD_SIZE", "1"))
@@ -384,7 +421,18 @@ def main():
                            "time_to_1pct_s": t_hit[0] if t_hit else None,
                            "steps_to_1pct": t_hit[1] if t_hit else None,
                            "wall_s": time.perf_counter() - t0}
+        # generalisation (Section 4.2): the trained Theta at perturbed x0
+        x0 = list(w.problem.x0)
+        rng = __import__("random").Random(w.seed)
+        cases = {f"scale{e:+.2f}": [(1.0 + e) * c for c in x0] for e in (-0.1, -0.05, 0.05, 0.1)}
+        cases["random0.05"] = [c * (1.0 + 0.05 * rng.gauss(0.0, 1.0)) for c in x0]
+        got = sa.generalisation(th, list(cases.values()))
+        out["generalisation"] = {
+            name: {"y0": g, "closed_form": P.workloads.bsb_y0(xc),
+                   "rel_err": abs(g - P.workloads.bsb_y0(xc)) / P.workloads.bsb_y0(xc)}
+            for (name, xc), g in zip(cases.items(), got)}
         del sa
+        out["multilevel"] = multilevel_run(P, w, target, args.accuracy_steps)
 
     if out is not None and not args.no_cpu_baseline:
         out["cpu_baseline"] = cpu_oracle_rate(P.workloads.WORKLOADS[args.workload],

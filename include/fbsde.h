@@ -196,6 +196,26 @@ fbsde_status fbsde_gemm_bf16(const void* A_dev, const void* B_dev, float* C_dev,
  * Adam moments are untouched, so training continues on the finer grid. */
 fbsde_status fbsde_set_level(fbsde_ctx* ctx, int N_level);
 
+/* Multilevel training (Section 3.2: coarse grids first, the number of Euler
+ * steps growing geometrically, e.g. 2, 4, 8, 16, 32 in Section 4.3): for
+ * level i = 0 .. n_levels-1, switch to N_levels[i] steps (as
+ * fbsde_set_level) and run steps_per_level[i] Adam steps (as
+ * fbsde_train_step) numbered first_step, first_step + 1, ... across all
+ * levels, so every step draws fresh Brownian increments.  Theta and the Adam
+ * moments carry over from level to level.
+ *   N_levels_host, steps_per_level_host: n_levels host ints (each level in
+ *     [1, N_max], each count >= 0); n_levels >= 1.
+ *   loss_trace_dev, y0_trace_dev: NULL or device arrays of
+ *     sum(steps_per_level) floats; step k of the schedule writes its loss and
+ *     Y_0 at index k.
+ * The context stays at the last level.  Enqueued on the context's stream with
+ * no host synchronisation; the arguments are checked before anything is
+ * enqueued (FBSDE_ERR_INVALID). */
+fbsde_status fbsde_train_schedule(fbsde_ctx* ctx, float* theta_dev, float* adam_m_dev, float* adam_v_dev,
+                                  const int* N_levels_host, const int* steps_per_level_host, int n_levels,
+                                  uint64_t first_step, float lr, float* loss_trace_dev,
+                                  float* y0_trace_dev);
+
 /* Replace the initial condition X_0 = x0 (D host doubles), e.g. for the
  * generalisation test of Section 4.2 (perturbed X_0, same Theta). */
 fbsde_status fbsde_set_x0(fbsde_ctx* ctx, const double* x0_host);

@@ -33,7 +33,7 @@ eps = 1e-8 with bias correction; uniform Delta t = T/N.
 """
 from __future__ import annotations
 
-from dataclasses import dataclass, field
+from dataclasses import dataclass, field, replace
 from typing import Optional
 
 import numpy as np
@@ -508,3 +508,25 @@ def train_step(problem: Problem, arch: Arch, theta, m, v, seed: int, step: int, 
     if arch.kind == "nais":
         theta = nais_project(theta, problem, arch)
     return ro.loss, ro.y0, theta, m, v
+
+
+def train_schedule(problem: Problem, arch: Arch, theta, m, v, seed: int, levels, steps,
+                   first_step: int, lr: float):
+    """Multilevel training (Section 3.2): the discretisation starts coarse and
+    is refined geometrically (Section 4.3 uses 2, 4, 8, 16 and 32 steps); at
+    level i the problem is solved on N = levels[i] Euler steps of
+    Delta t = T / N for steps[i] Adam iterations, and Theta and the Adam
+    moments carry over to the next level.  Step numbers continue across
+    levels (each iteration draws its own increments).  Returns
+    (losses, y0s, theta, m, v) with one loss and Y_0 per iteration."""
+    losses, y0s = [], []
+    step = first_step
+    for N, count in zip(levels, steps):
+        level = replace(problem, N=int(N))
+        for _ in range(int(count)):
+            loss, y0, theta, m, v = train_step(level, arch, theta, m, v, seed, step, lr)
+            losses.append(loss)
+            y0s.append(y0)
+            step += 1
+    return np.array(losses), np.array(y0s), theta, m, v
+

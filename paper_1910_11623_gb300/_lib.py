@@ -50,6 +50,8 @@ SIGNATURES = {
     "fbsde_gemm_bf16": (c_int, [c_void_p, c_void_p, c_void_p, c_int, c_int, c_int, c_int, c_int, c_int,
                                 c_int, c_void_p]),
     "fbsde_set_level": (c_int, [c_void_p, c_int]),
+    "fbsde_train_schedule": (c_int, [c_void_p, c_void_p, c_void_p, c_void_p, POINTER(c_int), POINTER(c_int), c_int,
+                                     c_uint64, c_float, c_void_p, c_void_p]),
     "fbsde_set_x0": (c_int, [c_void_p, POINTER(c_double)]),
     "fbsde_check_finite": (c_int, [c_void_p]),
     "fbsde_set_x0_device": (c_int, [c_void_p, c_void_p]),
@@ -173,6 +175,19 @@ def fbsde_gemm_bf16(A_ptr: int, B_ptr: int, C_ptr: int, rows: int, N: int, K: in
 
 def fbsde_set_level(ctx, N: int):
     check(load().fbsde_set_level(ctx, N), "fbsde_set_level", ctx)
+
+
+def fbsde_train_schedule(ctx, theta_ptr: int, m_ptr: int, v_ptr: int, levels, steps, first_step: int,
+                         lr: float, loss_trace_ptr: int = 0, y0_trace_ptr: int = 0):
+    n = len(levels)
+    if len(steps) != n:
+        raise ValueError("levels and steps must have the same length")
+    lv = (c_int * max(n, 1))(*levels)
+    st = (c_int * max(n, 1))(*steps)
+    check(load().fbsde_train_schedule(ctx, c_void_p(theta_ptr), c_void_p(m_ptr), c_void_p(v_ptr), lv, st, n,
+                                      first_step, lr, c_void_p(loss_trace_ptr or None),
+                                      c_void_p(y0_trace_ptr or None)),
+          "fbsde_train_schedule", ctx)
 
 
 def fbsde_set_x0(ctx, x0):

@@ -327,6 +327,32 @@ fbsde_status fbsde_set_level(fbsde_ctx* ctx, int N_level) {
     return FBSDE_OK;
 }
 
+fbsde_status fbsde_train_schedule(fbsde_ctx* ctx, float* theta_dev, float* adam_m_dev, float* adam_v_dev,
+                                  const int* N_levels_host, const int* steps_per_level_host, int n_levels,
+                                  uint64_t first_step, float lr, float* loss_trace_dev,
+                                  float* y0_trace_dev) {
+    if (!ctx) return FBSDE_ERR_INVALID;
+    if (!N_levels_host || !steps_per_level_host || n_levels < 1)
+        return set_err(ctx, FBSDE_ERR_INVALID, "N_levels_host and steps_per_level_host must hold n_levels >= 1 ints");
+    for (int i = 0; i < n_levels; ++i) {
+        if (N_levels_host[i] < 1 || N_levels_host[i] > ctx->N_max)
+            return set_err(ctx, FBSDE_ERR_INVALID, "level " + std::to_string(i) + ": N must be in [1, N_max]");
+        if (steps_per_level_host[i] < 0)
+            return set_err(ctx, FBSDE_ERR_INVALID, "level " + std::to_string(i) + ": step count must be >= 0");
+    }
+    if (first_step < 1) return set_err(ctx, FBSDE_ERR_INVALID, "step counts Adam steps from 1");
+    uint64_t step = first_step;
+    size_t k = 0;
+    for (int i = 0; i < n_levels; ++i) {
+        FBSDE_TRY(fbsde_set_level(ctx, N_levels_host[i]));
+        for (int s = 0; s < steps_per_level_host[i]; ++s, ++step, ++k)
+            FBSDE_TRY(fbsde_train_step(ctx, theta_dev, adam_m_dev, adam_v_dev, step, lr,
+                                       loss_trace_dev ? loss_trace_dev + k : nullptr,
+                                       y0_trace_dev ? y0_trace_dev + k : nullptr));
+    }
+    return FBSDE_OK;
+}
+
 fbsde_status fbsde_set_x0(fbsde_ctx* ctx, const double* x0_host) {
     if (!ctx || !x0_host) return set_err(ctx, FBSDE_ERR_INVALID, "ctx and x0_host must be non-NULL");
     for (int i = 0; i < ctx->D; ++i)

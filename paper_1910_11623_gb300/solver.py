@@ -160,6 +160,31 @@ class Solver:
     def set_x0(self, x0):
         L.fbsde_set_x0(self.ctx, list(x0))
 
+    def train_schedule(self, theta, m, v, levels, steps, first_step: int, lr: float):
+        """Multilevel training (Section 3.2): steps[i] Adam steps on a grid of
+        levels[i] Euler steps, Theta and the moments carried across levels.
+        Returns the per-step loss and Y_0 traces (device tensors)."""
+        total = int(sum(steps))
+        loss = torch.empty(max(total, 1), device=self.device)
+        y0 = torch.empty(max(total, 1), device=self.device)
+        L.fbsde_train_schedule(self.ctx, theta.data_ptr(), m.data_ptr(), v.data_ptr(), list(levels),
+                               list(steps), first_step, lr, loss.data_ptr(), y0.data_ptr())
+        self._level = int(levels[-1])
+        return loss[:total], y0[:total]
+
+    def generalisation(self, theta, x0s, iteration: int = 7 * 10**6):
+        """Y_0 = u(0, x0') of a trained Theta at other initial conditions
+        (Section 4.2: the parameters are not re-optimised).  Restores x0."""
+        out = []
+        try:
+            for k, x0 in enumerate(x0s):
+                self.set_x0(x0)
+                _, y0 = self.rollout_loss(theta, iteration + k)
+                out.append(float(y0.item()))
+        finally:
+            self.set_x0(self.problem.x0)
+        return out
+
     def check_finite(self):
         L.fbsde_check_finite(self.ctx)
 

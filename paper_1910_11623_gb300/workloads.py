@@ -55,3 +55,18 @@ WORKLOADS = {
 BSB_Y0_D100 = 77.10487946
 BSB_Y0_D10 = 7.710487946
 HJB_U00_D100 = 4.590162
+
+
+def bsb_y0(x0, r: float = 0.05, sigma: float = 0.4, T: float = 1.0) -> float:
+    """Closed form of the BSB problem (Section 4.1) at t = 0:
+    u(0, x) = exp((r + sigma^2) T) ||x||^2."""
+    import math
+    return math.exp((r + sigma * sigma) * T) * sum(float(v) * float(v) for v in x0)
+
+
+# Multilevel schedule of the measured workload (Section 3.2): grids of 4, 8,
+# 16 and 32 Euler steps for a fixed number of Adam steps each, then the
+# target grid of 64 steps.
+MULTILEVEL_LEVELS = (4, 8, 16, 32, 64)
+MULTILEVEL_COARSE_STEPS = 100
+

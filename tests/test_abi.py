@@ -103,3 +103,11 @@ def test_param_count_matches_the_oracle_layout(L):
 def test_status_strings(L):
     for s in range(7):
         assert L.fbsde_status_string(s)
+
+
+def test_schedule_rejects_a_null_context_without_a_gpu(L):
+    lib = L.load()
+    lv = (L.c_int * 2)(2, 4)
+    st = (L.c_int * 2)(1, 1)
+    rc = lib.fbsde_train_schedule(None, None, None, None, lv, st, 2, 1, 1e-3, None, None)
+    assert rc == L.FBSDE_ERR_INVALID

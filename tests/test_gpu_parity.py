@@ -234,3 +234,45 @@ def test_nonfinite_is_reported(P):
     assert ei.value.status == L.FBSDE_ERR_NONFINITE
     s.check_finite()  # the flag is cleared once reported
     s.close()
+
+
+@pytest.mark.parametrize("prec", ["fp32", "bf16"])
+def test_multilevel_schedule(P, prec):
+    # Section 3.2: levels 2 -> 4 -> 8 with Theta and the Adam moments carried
+    # over; the per-step loss / Y_0 traces and the final Theta follow the
+    # oracle's schedule
+    prob = P.ProblemSpec(kind="bsb", D=4, N=8, M=16, x0=[1.0, 0.5, 1.0, 0.5])
+    arch = P.ArchSpec(kind="resnet", width=32, depth=2, act="tanh", prec=prec)
+    s = _solver(P, prob, arch, seed=4, N_max=8)
+    th64, th = _theta_pair(P, s, prob, arch, 4)
+    m = torch.zeros_like(th); v = torch.zeros_like(th)
+    levels, steps = [2, 4, 8], [2, 1, 2]
+    loss, y0 = s.train_schedule(th, m, v, levels, steps, 1, 1e-3)
+    op, oa = oracle_specs(prob, arch)
+    z = np.zeros_like(th64)
+    lo, yo, tho, _, _ = F.train_schedule(op, oa, th64, z, z, 4, levels, steps, 1, 1e-3)
+    tol = TOL[prec]
+    assert rel_max(loss.cpu().numpy().astype(np.float64), lo) < tol
+    assert rel_max(y0.cpu().numpy().astype(np.float64), yo) < tol
+    assert rel_max(th.cpu().numpy().astype(np.float64), tho) < tol
+    assert s.problem_N == 8
+    s.close()
+
+
+def test_generalisation_perturbed_x0(P):
+    # Section 4.2: the same Theta evaluated at perturbed initial conditions
+    prob = P.ProblemSpec(kind="bsb", D=4, N=4, M=8, x0=[1.0, 0.5, 1.0, 0.5])
+    arch = P.ArchSpec(kind="fc", width=16, depth=2, act="tanh")
+    s = _solver(P, prob, arch, seed=5)
+    th64, th = _theta_pair(P, s, prob, arch, 5, perturb=0.05)
+    x0s = [[1.1, 0.5, 1.0, 0.5], [0.9, 0.45, 0.9, 0.45]]
+    got = s.generalisation(th, x0s, iteration=11)
+    from dataclasses import replace
+    op, oa = oracle_specs(prob, arch)
+    for k, x0 in enumerate(x0s):
+        want = F.rollout_loss(replace(op, x0=np.array(x0)), oa, th64, 5, 11 + k).y0
+        assert rel(got[k], want) < 1e-5
+    # x0 restored
+    _, y0 = s.rollout_loss(th, 3)
+    assert rel(y0.item(), F.rollout_loss(op, oa, th64, 5, 3).y0) < 1e-5
+    s.close()

@@ -363,3 +363,28 @@ def test_init_uses_the_init_key():
     th = F.init_params(p, arch, 9)
     z = philox.init_normals(9, th.size)
     assert th[0] == z[0] * np.sqrt(2.0 / (3 + 4))
+
+
+def test_train_schedule_is_levels_of_train_steps():
+    # Section 3.2: a multilevel schedule is plain training on successively
+    # finer grids, Theta and the Adam moments carried across; its first level
+    # must agree with single-level training on that grid, and the levels must
+    # really change Delta t (the losses on the coarse and the fine grid differ)
+    p = F.Problem(kind="bsb", D=3, N=8, M=4, x0=np.array([1.0, 0.5, 1.0]))
+    a = F.Arch(kind="fc", width=8, depth=1, act="tanh")
+    th0 = F.init_params(p, a, 3)
+    z = np.zeros_like(th0)
+    losses, y0s, th, m, v = F.train_schedule(p, a, th0, z, z, 3, [2, 4], [2, 1], 1, 1e-3)
+    assert losses.shape == (3,) and y0s.shape == (3,)
+    th_r, m_r, v_r = th0, z, z
+    want = []
+    for N, step in [(2, 1), (2, 2), (4, 3)]:
+        from dataclasses import replace
+        lo, _, th_r, m_r, v_r = F.train_step(replace(p, N=N), a, th_r, m_r, v_r, 3, step, 1e-3)
+        want.append(lo)
+    np.testing.assert_allclose(losses, want, rtol=0, atol=0)
+    np.testing.assert_array_equal(th, th_r)
+    # same Theta, same iteration, different grids: different losses
+    l2 = F.rollout_loss(replace(p, N=2), a, th0, 3, 9).loss
+    l4 = F.rollout_loss(replace(p, N=4), a, th0, 3, 9).loss
+    assert abs(l2 - l4) > 1e-6 * max(abs(l2), abs(l4))
