@@ -125,10 +125,15 @@ def measured_peaks():
             "sm_max_mhz": 2070.0}, "fallback"
 
 
+# Sources of the fused point-contraction kernels: a committed DRAM-traffic
+# figure is reported only while these are unchanged since its capture.
+KERNEL_SOURCES = ("fused.cu", "tc_common.cuh", "bf16_work.cuh")
+
+
 def source_hash() -> str:
     h = hashlib.sha256()
     csrc = os.path.join(ROOT, "paper_1910_11623_gb300", "csrc")
-    for f in sorted(os.listdir(csrc)):
+    for f in KERNEL_SOURCES:
         with open(os.path.join(csrc, f), "rb") as fh:
             h.update(f.encode() + fh.read())
     return h.hexdigest()[:16]

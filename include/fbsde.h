@@ -220,8 +220,11 @@ fbsde_status fbsde_train_schedule(fbsde_ctx* ctx, float* theta_dev, float* adam_
  * generalisation test of Section 4.2 (perturbed X_0, same Theta). */
 fbsde_status fbsde_set_x0(fbsde_ctx* ctx, const double* x0_host);
 
-/* Waits for the context's stream and reports FBSDE_ERR_NONFINITE if the last
- * loss or gradient produced by this context held a NaN or Inf. */
+/* Waits for the context's stream, then reports FBSDE_ERR_TIMEOUT if a
+ * tensor-core kernel of this context gave up a bounded wait (its tiles were
+ * left incomplete and the results since the last check are invalid), else
+ * FBSDE_ERR_NONFINITE if the last loss or gradient held a NaN or Inf.  Both
+ * flags are cleared by the call. */
 fbsde_status fbsde_check_finite(fbsde_ctx* ctx);
 
 /* Replace x0 from a device buffer (D floats), ordered on the context stream:

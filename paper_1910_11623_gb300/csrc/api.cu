@@ -407,9 +407,16 @@ uint64_t fbsde_launch_count(const fbsde_ctx* ctx) { return ctx ? ctx->n_launch :
 
 fbsde_status fbsde_check_finite(fbsde_ctx* ctx) {
     if (!ctx) return FBSDE_ERR_INVALID;
-    int flag = 0;
+    int flag = 0, timeout = 0;
+    int* terr = bf16_error_flag(ctx);
     FBSDE_CK(ctx, cudaMemcpyAsync(&flag, ctx->nonfinite, sizeof(int), cudaMemcpyDeviceToHost, ctx->stream));
+    if (terr) FBSDE_CK(ctx, cudaMemcpyAsync(&timeout, terr, sizeof(int), cudaMemcpyDeviceToHost, ctx->stream));
     FBSDE_CK(ctx, cudaStreamSynchronize(ctx->stream));
+    if (timeout) {
+        FBSDE_CK(ctx, cudaMemsetAsync(terr, 0, sizeof(int), ctx->stream));
+        if (flag) FBSDE_CK(ctx, cudaMemsetAsync(ctx->nonfinite, 0, sizeof(int), ctx->stream));
+        return set_err(ctx, FBSDE_ERR_TIMEOUT, "a tensor-core kernel gave up a bounded wait; results are invalid");
+    }
     if (flag) {
         FBSDE_CK(ctx, cudaMemsetAsync(ctx->nonfinite, 0, sizeof(int), ctx->stream));
         return set_err(ctx, FBSDE_ERR_NONFINITE, "a loss or gradient entry was NaN or Inf");

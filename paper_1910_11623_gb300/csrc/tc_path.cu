@@ -70,6 +70,8 @@ bool map3d(CUtensorMap* m, const void* base, uint64_t inner, uint64_t outer, uin
 
 constexpr int kColSplits = 296;
 
+int* bf16_error_flag(fbsde_ctx* c) { return c->bf ? c->bf->err : nullptr; }
+
 fbsde_status bf16_create(fbsde_ctx* c) {
     Bf16Work* b = new (std::nothrow) Bf16Work();
     if (!b) return set_err(c, FBSDE_ERR_OOM, "host allocation failed");
