@@ -14,10 +14,16 @@
 // tcgen05.mma instructions (K = 16 each) and commits stage releases and the
 // final accumulator; warps 2-5 (one thread per accumulator row) read the
 // accumulator with tcgen05.ld in 16-column slices and call the epilogue.
+// In TN mode the epilogue warps, idle during the main loop, can also sum the
+// columns of pair 0's A operand over the CTA's K range (a bias gradient is
+// the column sum of the same operand whose weight gradient this contracts):
+// they read each ring stage after it lands and release it with the MMA.
 // Every wait is bounded; a wait that gives up sets *args.err.
 #pragma once
 #include <cuda.h>
 #include <cuda_runtime.h>
+
+#include <cuda_bf16.h>
 
 #include "tc_common.cuh"
 
@@ -39,6 +45,13 @@ struct TcArgs {
     int N;       // output columns: multiple of 16, 16..256
     int kchunk;  // TN: K range per blockIdx.y, multiple of 64
     int* err;    // device flag set when a bounded wait gives up
+    // TN, optional (NULL: off): cs_part[blockIdx.y * rows + m] = sum over the
+    // CTA's K range of A(k, m) of pair 0, and cs_tpart the same weighted by
+    // t_k = floor(k / cs_M) * cs_dt (the time of point k)
+    float* cs_part;
+    float* cs_tpart;
+    int cs_M;
+    float cs_dt;
 };
 
 __host__ __device__ inline uint32_t tc_b_stage_bytes(int N) { return (uint32_t)((N + 63) / 64 * 64) * 128u; }
@@ -62,10 +75,13 @@ __global__ void __launch_bounds__(192, 1) tc_gemm_kernel(const __grid_constant__
     const uint32_t ncols = tc::tmem_cols_for(N);
     const int kbeg = TN ? (int)blockIdx.y * args.kchunk : 0;
 
+    // stage release: the MMA's commit, plus one arrival per epilogue warp
+    // when they read the stages for the column sums
+    const bool colsums = TN && args.cs_part != nullptr;
     if (threadIdx.x == 0) {
         for (int s = 0; s < kTcStages; ++s) {
             tc::mbar_init(&full[s], 1);
-            tc::mbar_init(&empty[s], 1);
+            tc::mbar_init(&empty[s], colsums ? 5 : 1);
         }
         tc::mbar_init(accf, 1);
         *abort_flag = 0;
@@ -161,7 +177,46 @@ __global__ void __launch_bounds__(192, 1) tc_gemm_kernel(const __grid_constant__
     } else {
         const int lg = warp & 3;  // TMEM lane group of this warp
         const int row = m0 + lg * 32 + lane;
-        const bool ok = tc::mbar_wait(accf, 0, tc::kWaitBudget);
+        bool cs_ok = true;
+        if (colsums) {
+            // feature fm of the tile: box fm / 64 of the stage's A slice, a
+            // [64 points x 64 features] block with the 128-byte swizzle
+            const int fm = lg * 32 + lane, box = fm >> 6, f = fm & 63;
+            const bool mine = row < args.rows;
+            float cs = 0.f, cst = 0.f;
+            int it = 0;
+            for (int q = 0; q < args.npairs && cs_ok; ++q) {
+                const int kend = min(args.pr[q].K, kbeg + args.kchunk);
+                for (int k0 = kbeg; k0 < kend; k0 += 64, ++it) {
+                    const int s = it % kTcStages;
+                    const uint32_t ph = (uint32_t)(it / kTcStages) & 1u;
+                    if (*abort_flag || !tc::mbar_wait(&full[s], ph, tc::kWaitBudget)) {
+                        cs_ok = false;
+                        break;
+                    }
+                    if (q == 0 && mine) {
+                        const uint8_t* sa = smem + (size_t)s * stage_bytes + box * 8192;
+                        const int nk = min(64, kend - k0);
+                        int n = k0 / args.cs_M, r = k0 % args.cs_M;
+                        for (int kk = 0; kk < nk; ++kk) {
+                            const uint32_t off = (uint32_t)kk * 128u + ((uint32_t)((f >> 3) ^ (kk & 7)) << 4) +
+                                                 (uint32_t)(f & 7) * 2u;
+                            const float v = __bfloat162float(*reinterpret_cast<const __nv_bfloat16*>(sa + off));
+                            cs += v;
+                            cst = fmaf((float)n * args.cs_dt, v, cst);
+                            if (++r == args.cs_M) { r = 0; ++n; }
+                        }
+                    }
+                    __syncwarp();
+                    if (lane == 0) tc::mbar_arrive(&empty[s]);
+                }
+            }
+            if (cs_ok && mine) {
+                args.cs_part[(size_t)blockIdx.y * args.rows + row] = cs;
+                if (args.cs_tpart) args.cs_tpart[(size_t)blockIdx.y * args.rows + row] = cst;
+            }
+        }
+        const bool ok = cs_ok && tc::mbar_wait(accf, 0, tc::kWaitBudget);
         if (ok) {
             tc::tc_fence_after();
             const uint32_t tbase = tmem + ((uint32_t)(lg * 32) << 16);

@@ -545,8 +545,12 @@ static fbsde_status colsum(fbsde_ctx* c, int cls, const void* X, bool is_bf16, i
 }
 
 // Weight gradient: out[r * ld + off + j] = sum over points of the TN pairs,
-// for output rows r < rows and columns j < ncols_store.
-static fbsde_status wgrad(fbsde_ctx* c, TcArgs a, int ncols_store, float* out, int ld, int off) {
+// for output rows r < rows and columns j < ncols_store.  With cs_out the same
+// launch also sums the columns of pair 0's A operand over all points
+// (cs_out[r * cs_ld], a bias gradient) and, with cst_out, the same sums
+// weighted by the point's time t (cst_out[r * cst_ld], the t column of W_in).
+static fbsde_status wgrad(fbsde_ctx* c, TcArgs a, int ncols_store, float* out, int ld, int off,
+                          float* cs_out = nullptr, int cs_ld = 1, float* cst_out = nullptr, int cst_ld = 1) {
     const size_t P = c->P();
     const int mblocks = (a.rows + 127) / 128;
     int want = (2 * 148 + mblocks - 1) / mblocks;
@@ -557,12 +561,34 @@ static fbsde_status wgrad(fbsde_ctx* c, TcArgs a, int ncols_store, float* out, i
         splits = (int)((P + kc - 1) / kc);
     }
     a.kchunk = (int)kc;
+    Bf16Work* b = c->bf;
+    const size_t cs_cap = (size_t)kColSplits * (rup(c->w, 16) + 16);
+    const bool cs = cs_out && (size_t)splits * a.rows * (cst_out ? 2 : 1) <= cs_cap;
+    if (cs) {
+        a.cs_part = b->colpart;
+        a.cs_tpart = cst_out ? b->colpart + (size_t)splits * a.rows : nullptr;
+        a.cs_M = c->M;
+        a.cs_dt = (float)(c->T / c->N);
+    }
     double flops = 0;
     for (int q = 0; q < a.npairs; ++q) flops += 2.0 * a.rows * (double)ncols_store * P;
     FBSDE_TRY(tc_launch<true>(c, PROF_WGRAD, a, splits, EpiPartB{c->part, a.rows, a.N}, flops));
     k_reduce_split<<<nblk((size_t)a.rows * ncols_store, 256), 256, 0, c->stream>>>(c->part, splits, a.rows, a.N,
                                                                                    ncols_store, out, ld, off);
     FBSDE_CK_LAUNCH(c);
+    if (cs) {
+        k_colsum_reduce<<<nblk((size_t)a.rows * 32, 256), 256, 0, c->stream>>>(b->colpart, splits, a.rows, cs_out,
+                                                                              cs_ld, 0);
+        FBSDE_CK_LAUNCH(c);
+        if (cst_out) {
+            k_colsum_reduce<<<nblk((size_t)a.rows * 32, 256), 256, 0, c->stream>>>(
+                b->colpart + (size_t)splits * a.rows, splits, a.rows, cst_out, cst_ld, 0);
+            FBSDE_CK_LAUNCH(c);
+        }
+    } else if (cs_out) {
+        // the partial sums do not fit the scratch: a separate pass over pair 0's A
+        return set_err(c, FBSDE_ERR_UNSUPPORTED, "column-sum scratch too small for this split");
+    }
     return FBSDE_OK;
 }
 
@@ -713,10 +739,10 @@ fbsde_status bf16_wgrad_tail(fbsde_ctx* c, const float* theta, float* grad) {
         TcArgs a = nt_args(c, w, w);
         add_pair(a, b->tAB[l], b->tH[l - 1], P);
         add_pair(a, b->tE[l], b->tHD[l - 1], P);
-        FBSDE_TRY(wgrad(c, a, w, nais ? c->gA[l] : grad + pl.W[l], w, 0));
-        FBSDE_TRY(colsum(c, PROF_WGRAD, b->ABb[l], true, wp, w, 0, nullptr, grad + pl.b[l], 1, 0));
+        // b_l (and for NAIS the t column of B_l) from the same pass over abar_l
+        FBSDE_TRY(wgrad(c, a, w, nais ? c->gA[l] : grad + pl.W[l], w, 0, grad + pl.b[l], 1,
+                        nais ? grad + pl.B[l] : nullptr, K0));
         if (nais) {
-            FBSDE_TRY(colsum(c, PROF_WGRAD, b->ABb[l], true, wp, w, 1, nullptr, grad + pl.B[l], K0, 0));
             TcArgs ax = nt_args(c, w, b->Dn);
             add_pair(ax, b->tAB[l], b->tX, P);
             add_pair(ax, b->tE[l], b->tV, P);
@@ -728,9 +754,8 @@ fbsde_status bf16_wgrad_tail(fbsde_ctx* c, const float* theta, float* grad) {
         TcArgs ax = nt_args(c, w, b->Dn);
         add_pair(ax, b->tAB[0], b->tX, P);
         add_pair(ax, b->tE[0], b->tV, P);
-        FBSDE_TRY(wgrad(c, ax, D, grad + pl.Win, K0, 1));
-        FBSDE_TRY(colsum(c, PROF_WGRAD, b->ABb[0], true, wp, w, 0, nullptr, grad + pl.bin, 1, 0));
-        FBSDE_TRY(colsum(c, PROF_WGRAD, b->ABb[0], true, wp, w, 1, nullptr, grad + pl.Win, K0, 0));
+        // b_in and the t column of W_in from the same pass over abar_0
+        FBSDE_TRY(wgrad(c, ax, D, grad + pl.Win, K0, 1, grad + pl.bin, 1, grad + pl.Win, K0));
     }
     // dw_o = sum_p alpha_p h_L(p) + h'_L(p);  db_o = sum_p alpha_p
     if (b->fused) {
