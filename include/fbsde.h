@@ -196,6 +196,32 @@ fbsde_status fbsde_gemm_bf16(const void* A_dev, const void* B_dev, float* C_dev,
  * Adam moments are untouched, so training continues on the finer grid. */
 fbsde_status fbsde_set_level(fbsde_ctx* ctx, int N_level);
 
+/* fbsde_train_step with the step number in device memory: *step_dev (one
+ * uint64, >= 1) keys the Brownian increments and Adam's bias correction as
+ * `step` does, and is incremented by one on the device at the end of the
+ * step.  Nothing of the step is then fixed on the host, so it can be captured
+ * once in a CUDA graph and replayed (fbsde_graph_capture).  Same outputs and
+ * errors as fbsde_train_step; step_dev must be non-NULL. */
+fbsde_status fbsde_train_step_dev(fbsde_ctx* ctx, float* theta_dev, float* adam_m_dev, float* adam_v_dev,
+                                  uint64_t* step_dev, float lr, float* loss_dev, float* y0_dev);
+
+/* A CUDA graph of `steps` consecutive fbsde_train_step_dev calls (the whole
+ * training step: paths, network, Z, loss, seeds, gradient, Adam), captured on
+ * the context's stream and instantiated.  Replaying it with
+ * fbsde_graph_launch enqueues the steps as one graph launch on that stream;
+ * each replay advances *step_dev by `steps`.  The graph bakes in the
+ * pointers, lr and the context's current level: capture again after
+ * fbsde_set_level or fbsde_set_x0.  Requires a context created on a
+ * non-default stream (FBSDE_ERR_UNSUPPORTED otherwise) and profiling off
+ * (FBSDE_ERR_INVALID).  *out owns the graph; free it with
+ * fbsde_graph_destroy before the context. */
+typedef struct fbsde_graph fbsde_graph;
+fbsde_status fbsde_graph_capture(fbsde_ctx* ctx, float* theta_dev, float* adam_m_dev, float* adam_v_dev,
+                                 uint64_t* step_dev, float lr, float* loss_dev, float* y0_dev, int steps,
+                                 fbsde_graph** out);
+fbsde_status fbsde_graph_launch(fbsde_graph* graph);
+fbsde_status fbsde_graph_destroy(fbsde_graph* graph);
+
 /* Multilevel training (Section 3.2: coarse grids first, the number of Euler
  * steps growing geometrically, e.g. 2, 4, 8, 16, 32 in Section 4.3): for
  * level i = 0 .. n_levels-1, switch to N_levels[i] steps (as

@@ -50,6 +50,12 @@ SIGNATURES = {
     "fbsde_gemm_bf16": (c_int, [c_void_p, c_void_p, c_void_p, c_int, c_int, c_int, c_int, c_int, c_int,
                                 c_int, c_void_p]),
     "fbsde_set_level": (c_int, [c_void_p, c_int]),
+    "fbsde_train_step_dev": (c_int, [c_void_p, c_void_p, c_void_p, c_void_p, c_void_p, c_float, c_void_p,
+                                     c_void_p]),
+    "fbsde_graph_capture": (c_int, [c_void_p, c_void_p, c_void_p, c_void_p, c_void_p, c_float, c_void_p,
+                                    c_void_p, c_int, POINTER(c_void_p)]),
+    "fbsde_graph_launch": (c_int, [c_void_p]),
+    "fbsde_graph_destroy": (c_int, [c_void_p]),
     "fbsde_train_schedule": (c_int, [c_void_p, c_void_p, c_void_p, c_void_p, POINTER(c_int), POINTER(c_int), c_int,
                                      c_uint64, c_float, c_void_p, c_void_p]),
     "fbsde_set_x0": (c_int, [c_void_p, POINTER(c_double)]),
@@ -171,6 +177,32 @@ def fbsde_gemm_bf16(A_ptr: int, B_ptr: int, C_ptr: int, rows: int, N: int, K: in
                     ldc: int, trans: int, stream: int):
     check(load().fbsde_gemm_bf16(c_void_p(A_ptr), c_void_p(B_ptr), c_void_p(C_ptr), rows, N, K, lda, ldb, ldc,
                                  trans, c_void_p(stream or None)), "fbsde_gemm_bf16")
+
+
+def fbsde_train_step_dev(ctx, theta_ptr: int, m_ptr: int, v_ptr: int, step_ptr: int, lr: float,
+                         loss_ptr: int = 0, y0_ptr: int = 0):
+    check(load().fbsde_train_step_dev(ctx, c_void_p(theta_ptr), c_void_p(m_ptr), c_void_p(v_ptr),
+                                      c_void_p(step_ptr), lr, c_void_p(loss_ptr or None),
+                                      c_void_p(y0_ptr or None)),
+          "fbsde_train_step_dev", ctx)
+
+
+def fbsde_graph_capture(ctx, theta_ptr: int, m_ptr: int, v_ptr: int, step_ptr: int, lr: float,
+                        loss_ptr: int, y0_ptr: int, steps: int):
+    out = c_void_p()
+    check(load().fbsde_graph_capture(ctx, c_void_p(theta_ptr), c_void_p(m_ptr), c_void_p(v_ptr),
+                                     c_void_p(step_ptr), lr, c_void_p(loss_ptr or None),
+                                     c_void_p(y0_ptr or None), steps, ctypes.byref(out)),
+          "fbsde_graph_capture", ctx)
+    return out
+
+
+def fbsde_graph_launch(graph, ctx=None):
+    check(load().fbsde_graph_launch(graph), "fbsde_graph_launch", ctx)
+
+
+def fbsde_graph_destroy(graph):
+    load().fbsde_graph_destroy(graph)
 
 
 def fbsde_set_level(ctx, N: int):

@@ -8,9 +8,21 @@
 
 namespace fbsde {
 
+// The bias corrections 1 / (1 - beta^step) are formed on the device (FP64,
+// once per block) from the step passed by value or read from step_dev, so a
+// step replayed from a CUDA graph computes exactly what a direct call does.
 __global__ void k_adam(size_t n, float* __restrict__ theta, const float* __restrict__ g,
-                       float* __restrict__ m, float* __restrict__ v, float lr, float b1, float b2,
-                       float inv_bc1, float inv_bc2, float eps) {
+                       float* __restrict__ m, float* __restrict__ v, float lr, double b1d, double b2d,
+                       uint64_t step_host, const uint64_t* __restrict__ step_dev, float eps) {
+    __shared__ float inv_bc[2];
+    const float b1 = (float)b1d, b2 = (float)b2d;
+    if (threadIdx.x == 0) {
+        const double step = (double)(step_dev ? *step_dev : step_host);
+        inv_bc[0] = (float)(1.0 / (1.0 - pow(b1d, step)));
+        inv_bc[1] = (float)(1.0 / (1.0 - pow(b2d, step)));
+    }
+    __syncthreads();
+    const float inv_bc1 = inv_bc[0], inv_bc2 = inv_bc[1];
     size_t i = (size_t)blockIdx.x * blockDim.x + threadIdx.x;
     if (i >= n) return;
     const float gi = g[i];
@@ -23,14 +35,19 @@ __global__ void k_adam(size_t n, float* __restrict__ theta, const float* __restr
 
 fbsde_status launch_adam(fbsde_ctx* ctx, float* theta, const float* grad, float* m, float* v,
                          uint64_t step, float lr) {
-    const double b1 = 0.9, b2 = 0.999;
-    const double bc1 = 1.0 - std::pow(b1, (double)step);
-    const double bc2 = 1.0 - std::pow(b2, (double)step);
     const size_t n = ctx->pl.total;
     const int tok = prof_begin(ctx, PROF_OTHER);
-    k_adam<<<(unsigned)((n + 255) / 256), 256, 0, ctx->stream>>>(
-        n, theta, grad, m, v, lr, (float)b1, (float)b2, (float)(1.0 / bc1), (float)(1.0 / bc2), 1e-8f);
+    k_adam<<<(unsigned)((n + 255) / 256), 256, 0, ctx->stream>>>(n, theta, grad, m, v, lr, 0.9, 0.999, step,
+                                                                 ctx->step_dev, 1e-8f);
     prof_end(ctx, PROF_OTHER, tok, 0.0);
+    FBSDE_CK_LAUNCH(ctx);
+    return FBSDE_OK;
+}
+
+__global__ void k_step_advance(uint64_t* step) { *step += 1; }
+
+fbsde_status launch_step_advance(fbsde_ctx* ctx, uint64_t* step) {
+    k_step_advance<<<1, 1, 0, ctx->stream>>>(step);
     FBSDE_CK_LAUNCH(ctx);
     return FBSDE_OK;
 }

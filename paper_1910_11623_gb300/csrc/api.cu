@@ -288,6 +288,87 @@ fbsde_status fbsde_train_step(fbsde_ctx* ctx, float* theta_dev, float* adam_m_de
     return FBSDE_OK;
 }
 
+fbsde_status fbsde_train_step_dev(fbsde_ctx* ctx, float* theta_dev, float* adam_m_dev, float* adam_v_dev,
+                                  uint64_t* step_dev, float lr, float* loss_dev, float* y0_dev) {
+    if (!ctx || !theta_dev || !adam_m_dev || !adam_v_dev || !step_dev)
+        return set_err(ctx, FBSDE_ERR_INVALID, "ctx, theta_dev, adam_m_dev, adam_v_dev, step_dev must be non-NULL");
+    if (!(lr > 0) || !std::isfinite(lr)) return set_err(ctx, FBSDE_ERR_INVALID, "lr must be finite and > 0");
+    ctx->step_dev = step_dev;
+    // the host step value is unused while step_dev is set; 1 passes the checks
+    fbsde_status st = fbsde_train_step(ctx, theta_dev, adam_m_dev, adam_v_dev, 1, lr, loss_dev, y0_dev);
+    ctx->step_dev = nullptr;
+    if (st != FBSDE_OK) return st;
+    return launch_step_advance(ctx, step_dev);
+}
+
+}  // extern "C"
+
+struct fbsde_graph {
+    fbsde_ctx* ctx = nullptr;
+    cudaGraph_t graph = nullptr;
+    cudaGraphExec_t exec = nullptr;
+};
+
+extern "C" {
+
+fbsde_status fbsde_graph_capture(fbsde_ctx* ctx, float* theta_dev, float* adam_m_dev, float* adam_v_dev,
+                                 uint64_t* step_dev, float lr, float* loss_dev, float* y0_dev, int steps,
+                                 fbsde_graph** out) {
+    if (!ctx || !out) return set_err(ctx, FBSDE_ERR_INVALID, "ctx and out must be non-NULL");
+    *out = nullptr;
+    if (steps < 1) return set_err(ctx, FBSDE_ERR_INVALID, "steps must be >= 1");
+    if (!ctx->stream)
+        return set_err(ctx, FBSDE_ERR_UNSUPPORTED, "graph capture needs a context created on a non-default stream");
+    if (ctx->prof.on) return set_err(ctx, FBSDE_ERR_INVALID, "disable profiling before capturing a graph");
+    if (!theta_dev || !adam_m_dev || !adam_v_dev || !step_dev)
+        return set_err(ctx, FBSDE_ERR_INVALID, "theta_dev, adam_m_dev, adam_v_dev, step_dev must be non-NULL");
+    cudaError_t e = cudaStreamBeginCapture(ctx->stream, cudaStreamCaptureModeThreadLocal);
+    if (e != cudaSuccess) return set_err(ctx, FBSDE_ERR_CUDA, std::string("cudaStreamBeginCapture: ") + cudaGetErrorString(e));
+    fbsde_status st = FBSDE_OK;
+    for (int k = 0; k < steps && st == FBSDE_OK; ++k)
+        st = fbsde_train_step_dev(ctx, theta_dev, adam_m_dev, adam_v_dev, step_dev, lr, loss_dev, y0_dev);
+    cudaGraph_t graph = nullptr;
+    e = cudaStreamEndCapture(ctx->stream, &graph);
+    if (st != FBSDE_OK) {
+        if (graph) cudaGraphDestroy(graph);
+        return st;
+    }
+    if (e != cudaSuccess) {
+        if (graph) cudaGraphDestroy(graph);
+        return set_err(ctx, FBSDE_ERR_CUDA, std::string("cudaStreamEndCapture: ") + cudaGetErrorString(e));
+    }
+    cudaGraphExec_t exec = nullptr;
+    e = cudaGraphInstantiate(&exec, graph, 0);
+    if (e != cudaSuccess) {
+        cudaGraphDestroy(graph);
+        return set_err(ctx, FBSDE_ERR_CUDA, std::string("cudaGraphInstantiate: ") + cudaGetErrorString(e));
+    }
+    fbsde_graph* g = new (std::nothrow) fbsde_graph();
+    if (!g) {
+        cudaGraphExecDestroy(exec);
+        cudaGraphDestroy(graph);
+        return set_err(ctx, FBSDE_ERR_OOM, "host allocation failed");
+    }
+    g->ctx = ctx; g->graph = graph; g->exec = exec;
+    *out = g;
+    return FBSDE_OK;
+}
+
+fbsde_status fbsde_graph_launch(fbsde_graph* graph) {
+    if (!graph) return FBSDE_ERR_INVALID;
+    cudaError_t e = cudaGraphLaunch(graph->exec, graph->ctx->stream);
+    if (e != cudaSuccess) return set_err(graph->ctx, FBSDE_ERR_CUDA, std::string("cudaGraphLaunch: ") + cudaGetErrorString(e));
+    return FBSDE_OK;
+}
+
+fbsde_status fbsde_graph_destroy(fbsde_graph* graph) {
+    if (!graph) return FBSDE_OK;
+    cudaError_t e1 = cudaGraphExecDestroy(graph->exec);
+    cudaError_t e2 = cudaGraphDestroy(graph->graph);
+    delete graph;
+    return (e1 == cudaSuccess && e2 == cudaSuccess) ? FBSDE_OK : FBSDE_ERR_CUDA;
+}
+
 fbsde_status fbsde_rollout_detail(fbsde_ctx* ctx, const float* theta_dev, uint64_t iter, float* Y_dev,
                                   float* Z_dev, float* path_loss_dev) {
     if (!ctx || !theta_dev) return set_err(ctx, FBSDE_ERR_INVALID, "ctx and theta_dev must be non-NULL");

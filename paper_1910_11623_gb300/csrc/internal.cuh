@@ -70,6 +70,10 @@ struct fbsde_ctx {
     double h = 1, eps = 0.01, delta = 1;
     uint64_t seed = 0;
     cudaStream_t stream = nullptr;
+    // When set, the iteration / Adam step number is read from this device
+    // word by the kernels (a step captured in a CUDA graph) instead of being
+    // passed by value.
+    const uint64_t* step_dev = nullptr;
     fbsde::ParamLayout pl;
     std::string err;
 
@@ -183,6 +187,8 @@ inline float layer_scale(const fbsde_ctx* c, int l) {
 }
 
 // Adam (adam.cu).
+// ++*step on the device (end of a device-numbered training step).
+fbsde_status launch_step_advance(fbsde_ctx* ctx, uint64_t* step);
 fbsde_status launch_adam(fbsde_ctx* ctx, float* theta, const float* grad, float* m, float* v,
                          uint64_t step, float lr);
 

@@ -17,8 +17,9 @@ namespace fbsde {
 // drawing Delta W_n from Philox counter (q, n, m, iter) and updating
 // X_{n+1} = X_n + sigma(X_n) Delta W_n.  Layout: row n * M + m, column d.
 __global__ void k_paths(ProblemDev pd, const float* __restrict__ x0, uint32_t k0, uint32_t k1,
-                        uint32_t it, float* __restrict__ X, float* __restrict__ dW,
-                        __nv_bfloat16* __restrict__ Xb, int ldb) {
+                        uint32_t it_host, const uint64_t* __restrict__ it_dev, float* __restrict__ X,
+                        float* __restrict__ dW, __nv_bfloat16* __restrict__ Xb, int ldb) {
+    const uint32_t it = it_dev ? (uint32_t)*it_dev : it_host;
     const int Q = (pd.D + 3) >> 2;
     const long idx = (long)blockIdx.x * blockDim.x + threadIdx.x;
     if (idx >= (long)pd.M * Q) return;
@@ -72,8 +73,8 @@ fbsde_status launch_paths(fbsde_ctx* ctx, uint64_t iter) {
     const int bs = 128;
     const int tok = prof_begin(ctx, PROF_OTHER);
     k_paths<<<(unsigned)((n + bs - 1) / bs), bs, 0, ctx->stream>>>(
-        pd, ctx->x0_dev, (uint32_t)ctx->seed, (uint32_t)(ctx->seed >> 32), (uint32_t)iter, ctx->X,
-        ctx->dW, ctx->Xb_op, ctx->ld_op);
+        pd, ctx->x0_dev, (uint32_t)ctx->seed, (uint32_t)(ctx->seed >> 32), (uint32_t)iter, ctx->step_dev,
+        ctx->X, ctx->dW, ctx->Xb_op, ctx->ld_op);
     prof_end(ctx, PROF_OTHER, tok, 0.0);
     FBSDE_CK_LAUNCH(ctx);
     return FBSDE_OK;

@@ -160,6 +160,19 @@ class Solver:
     def set_x0(self, x0):
         L.fbsde_set_x0(self.ctx, list(x0))
 
+    def train_step_dev(self, theta, m, v, step_dev, lr: float = 1e-3, loss=None, y0=None):
+        """One training step numbered by the device word step_dev (int64
+        tensor of one element), which the step advances by one."""
+        loss = loss if loss is not None else torch.empty(1, device=self.device)
+        y0 = y0 if y0 is not None else torch.empty(1, device=self.device)
+        L.fbsde_train_step_dev(self.ctx, theta.data_ptr(), m.data_ptr(), v.data_ptr(), step_dev.data_ptr(), lr,
+                               loss.data_ptr(), y0.data_ptr())
+        return loss, y0
+
+    def capture_train_steps(self, theta, m, v, step_dev, lr: float = 1e-3, steps: int = 1):
+        """CUDA graph of `steps` training steps (see TrainGraph)."""
+        return TrainGraph(self, theta, m, v, step_dev, lr, steps)
+
     def train_schedule(self, theta, m, v, levels, steps, first_step: int, lr: float):
         """Multilevel training (Section 3.2): steps[i] Adam steps on a grid of
         levels[i] Euler steps, Theta and the moments carried across levels.
@@ -187,6 +200,36 @@ class Solver:
 
     def check_finite(self):
         L.fbsde_check_finite(self.ctx)
+
+
+class TrainGraph:
+    """A captured, instantiated CUDA graph of consecutive training steps of a
+    Solver (fbsde_graph_capture); launch() replays them on the solver's
+    stream and advances the device step counter.  The loss and Y_0 of the
+    last replayed step are in .loss and .y0."""
+
+    def __init__(self, solver: "Solver", theta, m, v, step_dev, lr: float, steps: int):
+        self.solver, self.steps = solver, steps
+        self._keep = (theta, m, v, step_dev)
+        self.loss = torch.empty(1, device=solver.device)
+        self.y0 = torch.empty(1, device=solver.device)
+        self.handle = L.fbsde_graph_capture(solver.ctx, theta.data_ptr(), m.data_ptr(), v.data_ptr(),
+                                            step_dev.data_ptr(), lr, self.loss.data_ptr(), self.y0.data_ptr(),
+                                            steps)
+
+    def launch(self):
+        L.fbsde_graph_launch(self.handle, self.solver.ctx)
+
+    def close(self):
+        if self.handle:
+            L.fbsde_graph_destroy(self.handle)
+            self.handle = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
 
 
 def philox4x32_10(ctr: torch.Tensor, key0: int, key1: int) -> torch.Tensor:

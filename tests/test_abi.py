@@ -111,3 +111,13 @@ def test_schedule_rejects_a_null_context_without_a_gpu(L):
     st = (L.c_int * 2)(1, 1)
     rc = lib.fbsde_train_schedule(None, None, None, None, lv, st, 2, 1, 1e-3, None, None)
     assert rc == L.FBSDE_ERR_INVALID
+
+
+def test_graph_entry_points_reject_null_arguments_without_a_gpu(L):
+    lib = L.load()
+    out = L.c_void_p()
+    assert lib.fbsde_graph_capture(None, None, None, None, None, 1e-3, None, None, 1,
+                                   L.ctypes.byref(out)) == L.FBSDE_ERR_INVALID
+    assert lib.fbsde_graph_launch(None) == L.FBSDE_ERR_INVALID
+    assert lib.fbsde_graph_destroy(None) == L.FBSDE_OK
+    assert lib.fbsde_train_step_dev(None, None, None, None, None, 1e-3, None, None) == L.FBSDE_ERR_INVALID

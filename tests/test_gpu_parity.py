@@ -276,3 +276,36 @@ def test_generalisation_perturbed_x0(P):
     _, y0 = s.rollout_loss(th, 3)
     assert rel(y0.item(), F.rollout_loss(op, oa, th64, 5, 3).y0) < 1e-5
     s.close()
+
+
+@pytest.mark.parametrize("prec", ["fp32", "bf16"])
+def test_graph_replay_is_the_same_training(P, prec):
+    # the whole step captured once in a CUDA graph (device step counter)
+    # reproduces direct calls bit for bit, and follows the oracle
+    prob = P.ProblemSpec(kind="bsb", D=6, N=4, M=32, x0=[1.0, 0.5] * 3)
+    arch = P.ArchSpec(kind="resnet", width=32, depth=2, act="tanh", prec=prec)
+    stream = torch.cuda.Stream()
+    s = P.Solver(prob, arch, seed=6, stream=stream)
+    th64, th = _theta_pair(P, s, prob, arch, 6)
+    th_a, th_b = th.clone(), th.clone()
+    m_a, v_a = torch.zeros_like(th), torch.zeros_like(th)
+    m_b, v_b = torch.zeros_like(th), torch.zeros_like(th)
+    with torch.cuda.stream(stream):
+        for step in range(1, 5):
+            la, ya = s.train_step(th_a, m_a, v_a, step, 1e-3)
+        step_dev = torch.ones(1, dtype=torch.int64, device="cuda")
+        g = s.capture_train_steps(th_b, m_b, v_b, step_dev, 1e-3, steps=2)
+        g.launch()
+        g.launch()
+    stream.synchronize()
+    assert int(step_dev.item()) == 5
+    assert torch.equal(th_a, th_b) and torch.equal(m_a, m_b) and torch.equal(v_a, v_b)
+    assert g.loss.item() == la.item() and g.y0.item() == ya.item()
+    op, oa = oracle_specs(prob, arch)
+    z = np.zeros_like(th64)
+    mo, vo, tho = z, z, th64
+    for step in range(1, 5):
+        _, _, tho, mo, vo = F.train_step(op, oa, tho, mo, vo, 6, step, 1e-3)
+    assert rel_max(th_b.cpu().numpy().astype(np.float64), tho) < TOL[prec]
+    g.close()
+    s.close()
