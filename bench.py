@@ -51,6 +51,8 @@ def parse_args():
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--loss-steps", type=int, default=20,
                     help="timed loss-only evaluations (forward sweep + residuals), 0: skip")
+    ap.add_argument("--batched-steps", type=int, default=3,
+                    help="timed group steps of the 32 uneven instances (0: skip)")
     ap.add_argument("--M", type=int, default=0,
                     help="override the number of paths (small cases for profiler captures)")
     return ap.parse_args()
@@ -206,6 +208,71 @@ def time_steps(solver, theta, m, v, first_step, K, lr):
     e1.record(st)
     e1.synchronize()
     return e0.elapsed_time(e1)
+
+
+def batched_run(P, steps: int, lr: float):
+    """32 independent uneven instances (half BSB, half HJB; D, N, M, width
+    drawn with a seed) trained together: each instance's training step on
+    its own stream, the group step captured as one CUDA graph, the SM split
+    between the instances autotuned.  Against: the same instances trained
+    one after another with direct calls."""
+    import torch
+    from paper_1910_11623_gb300 import _lib as L
+    ws = P.workloads.batched_instances()
+    solvers, th, mm, vv, streams = [], [], [], [], []
+    for w in ws:
+        # a stream of its own per instance (torch's stream pool would hand out shared ones)
+        st = torch.cuda.ExternalStream(L.fbsde_stream_create())
+        streams.append(st)
+        s = P.Solver(w.problem, w.arch, seed=w.seed, stream=st)
+        t = s.init_params()
+        solvers.append(s); th.append(t); mm.append(torch.zeros_like(t)); vv.append(torch.zeros_like(t))
+    n = len(solvers)
+    # one after another, direct calls on one stream
+    seq = torch.cuda.Stream()
+    for s, t, m, v in zip(solvers, th, mm, vv):
+        with torch.cuda.stream(seq):
+            s.train_step(t, m, v, 1, lr)
+    torch.cuda.synchronize()
+    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    per = []
+    for s, t, m, v in zip(solvers, th, mm, vv):
+        e0.record(s.stream)
+        for k in range(steps):
+            s.train_step(t, m, v, 2 + k, lr)
+        e1.record(s.stream)
+        e1.synchronize()
+        per.append(e0.elapsed_time(e1) / steps)
+    seq_ms = sum(per)
+    G = P.Group(solvers)
+    caps, tune_ms, _ = G.autotune(th, lr, trial_steps=1)
+    step_dev = torch.full((n,), 2 + steps, dtype=torch.int64, device="cuda")
+    graph = G.capture(th, mm, vv, step_dev, lr, steps=1)
+    graph.launch()
+    torch.cuda.synchronize()
+    e0.record(G.stream)
+    for _ in range(steps):
+        graph.launch()
+    e1.record(G.stream)
+    e1.synchronize()
+    g_ms = e0.elapsed_time(e1) / steps
+    pts = sum(w.problem.M * (w.problem.N + 1) for w in ws)
+    res = {"instances": n, "points_per_round": pts,
+           "shapes": [[w.problem.kind, w.problem.D, w.problem.N, w.problem.M, w.arch.width] for w in ws],
+           "sequential_ms_per_round": seq_ms, "grouped_ms_per_round": g_ms,
+           "speedup_grouped_vs_sequential": seq_ms / g_ms,
+           "instance_steps_per_s": n / (g_ms / 1000.0), "autotune": {"caps": caps, "ms_per_step": tune_ms},
+           "timing": f"{steps} group steps replayed from one CUDA graph per step, after one warm replay"}
+    graph.close()
+    G.close()
+    for s in solvers:
+        s.close()
+    torch.cuda.synchronize()
+    for st in streams:
+        L.fbsde_stream_destroy(st.cuda_stream)
+    del solvers, th, mm, vv
+    torch.cuda.empty_cache()
+    return res
 
 
 def multilevel_run(P, w, target, max_steps):
@@ -465,6 +532,12 @@ def main():
             for (name, xc), g in zip(cases.items(), got)}
         del sa
         out["multilevel"] = multilevel_run(P, w, target, args.accuracy_steps)
+
+    if out is not None and args.batched_steps > 0 and world == 1:
+        try:
+            out["batched"] = batched_run(P, args.batched_steps, w.lr)
+        except Exception as exc:  # report, keep the main line
+            out["batched"] = {"error": f"{type(exc).__name__}: {exc}"}
 
     if out is not None and not args.no_cpu_baseline:
         out["cpu_baseline"] = cpu_oracle_rate(P.workloads.WORKLOADS[args.workload],

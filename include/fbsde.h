@@ -222,6 +222,55 @@ fbsde_status fbsde_graph_capture(fbsde_ctx* ctx, float* theta_dev, float* adam_m
 fbsde_status fbsde_graph_launch(fbsde_graph* graph);
 fbsde_status fbsde_graph_destroy(fbsde_graph* graph);
 
+/* Groups of independent instances (many FBSDEs of uneven D, N, M, width
+ * trained at once; the paper trains one at a time, this is a batching layer
+ * over its training step).
+ *
+ * fbsde_group_create: a group over n >= 1 distinct contexts, each created on
+ * a non-default stream; `cuda_stream` (non-default) is the group's stream,
+ * where group steps fork and join.  Instances run concurrently as far as
+ * their streams differ (contexts sharing a stream run one after another).
+ * The group does not own the contexts; destroy it before them.
+ * FBSDE_ERR_INVALID on NULLs or repeated contexts.
+ *
+ * fbsde_group_train_step: one training step of every instance (as
+ * fbsde_train_step_dev): theta, m, v are n device pointers (host array),
+ * step_dev a device array of n uint64 step counters, loss_dev / y0_dev NULL
+ * or device arrays of n floats (instance i writes index i).  The instances
+ * run concurrently on their streams; on return the group's stream is ordered
+ * after all of them.
+ *
+ * fbsde_group_capture: `steps` group steps captured on the group's stream as
+ * one CUDA graph (fbsde_graph_launch replays it with a single launch).
+ *
+ * fbsde_set_grid_cap: at most `ctas` CTAs (0: one per SM) for the context's
+ * fused per-tile kernels, so that the instances of a group share the SMs.
+ *
+ * fbsde_group_autotune: times `trial_steps` group steps (after one warm-up)
+ * for each candidate split of the SMs (all SMs for every instance; SMs in
+ * proportion to each instance's contraction work; half of the SMs each) on
+ * scratch copies of theta (Adam moments zero, step 1), keeps the fastest
+ * split in the contexts and writes each instance's cap to caps_out (n ints)
+ * and the step time in ms to *ms_out (may be NULL).  Synchronises the group's
+ * stream; the caller's theta is only read. */
+typedef struct fbsde_group fbsde_group;
+/* A new non-blocking CUDA stream (cudaStream_t in *out), for callers whose
+ * framework hands out pooled streams, so that every instance of a group can
+ * have one of its own; fbsde_stream_destroy frees it (NULL accepted). */
+fbsde_status fbsde_stream_create(void** out);
+fbsde_status fbsde_stream_destroy(void* stream);
+fbsde_status fbsde_group_create(fbsde_ctx* const* ctxs, int n, void* cuda_stream, fbsde_group** out);
+fbsde_status fbsde_group_destroy(fbsde_group* group);
+fbsde_status fbsde_group_train_step(fbsde_group* group, float* const* theta_dev, float* const* adam_m_dev,
+                                    float* const* adam_v_dev, uint64_t* step_dev, float lr, float* loss_dev,
+                                    float* y0_dev);
+fbsde_status fbsde_group_capture(fbsde_group* group, float* const* theta_dev, float* const* adam_m_dev,
+                                 float* const* adam_v_dev, uint64_t* step_dev, float lr, float* loss_dev,
+                                 float* y0_dev, int steps, fbsde_graph** out);
+fbsde_status fbsde_set_grid_cap(fbsde_ctx* ctx, int ctas);
+fbsde_status fbsde_group_autotune(fbsde_group* group, const float* const* theta_dev, float lr, int trial_steps,
+                                  int* caps_out, float* ms_out);
+
 /* Multilevel training (Section 3.2: coarse grids first, the number of Euler
  * steps growing geometrically, e.g. 2, 4, 8, 16, 32 in Section 4.3): for
  * level i = 0 .. n_levels-1, switch to N_levels[i] steps (as

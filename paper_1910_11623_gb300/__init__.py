@@ -6,5 +6,5 @@ and its Theta-gradient, and Adam.  This package only marshals arguments
 (`_lib`, same names as the C entry points) and manages torch-owned buffers
 (`solver`).
 """
-from .solver import ArchSpec, ProblemSpec, RolloutLoss, Solver, param_count, philox4x32_10  # noqa: F401
+from .solver import ArchSpec, Group, ProblemSpec, RolloutLoss, Solver, TrainGraph, param_count, philox4x32_10  # noqa: F401
 from . import workloads  # noqa: F401

@@ -55,6 +55,17 @@ SIGNATURES = {
     "fbsde_graph_capture": (c_int, [c_void_p, c_void_p, c_void_p, c_void_p, c_void_p, c_float, c_void_p,
                                     c_void_p, c_int, POINTER(c_void_p)]),
     "fbsde_graph_launch": (c_int, [c_void_p]),
+    "fbsde_group_create": (c_int, [POINTER(c_void_p), c_int, c_void_p, POINTER(c_void_p)]),
+    "fbsde_group_destroy": (c_int, [c_void_p]),
+    "fbsde_group_train_step": (c_int, [c_void_p, POINTER(c_void_p), POINTER(c_void_p), POINTER(c_void_p),
+                                       c_void_p, c_float, c_void_p, c_void_p]),
+    "fbsde_group_capture": (c_int, [c_void_p, POINTER(c_void_p), POINTER(c_void_p), POINTER(c_void_p),
+                                    c_void_p, c_float, c_void_p, c_void_p, c_int, POINTER(c_void_p)]),
+    "fbsde_set_grid_cap": (c_int, [c_void_p, c_int]),
+    "fbsde_stream_create": (c_int, [POINTER(c_void_p)]),
+    "fbsde_stream_destroy": (c_int, [c_void_p]),
+    "fbsde_group_autotune": (c_int, [c_void_p, POINTER(c_void_p), c_float, c_int, POINTER(c_int),
+                                     POINTER(c_float)]),
     "fbsde_graph_destroy": (c_int, [c_void_p]),
     "fbsde_train_schedule": (c_int, [c_void_p, c_void_p, c_void_p, c_void_p, POINTER(c_int), POINTER(c_int), c_int,
                                      c_uint64, c_float, c_void_p, c_void_p]),
@@ -203,6 +214,63 @@ def fbsde_graph_launch(graph, ctx=None):
 
 def fbsde_graph_destroy(graph):
     load().fbsde_graph_destroy(graph)
+
+
+def _ptr_array(ptrs):
+    return (c_void_p * max(len(ptrs), 1))(*[c_void_p(p) for p in ptrs])
+
+
+def fbsde_group_create(ctxs, stream: int):
+    arr = (c_void_p * len(ctxs))(*ctxs)
+    out = c_void_p()
+    check(load().fbsde_group_create(arr, len(ctxs), c_void_p(stream or None), ctypes.byref(out)),
+          "fbsde_group_create")
+    return out
+
+
+def fbsde_group_destroy(group):
+    load().fbsde_group_destroy(group)
+
+
+def fbsde_group_train_step(group, theta_ptrs, m_ptrs, v_ptrs, step_ptr: int, lr: float, loss_ptr: int = 0,
+                           y0_ptr: int = 0):
+    check(load().fbsde_group_train_step(group, _ptr_array(theta_ptrs), _ptr_array(m_ptrs), _ptr_array(v_ptrs),
+                                        c_void_p(step_ptr), lr, c_void_p(loss_ptr or None),
+                                        c_void_p(y0_ptr or None)),
+          "fbsde_group_train_step")
+
+
+def fbsde_group_capture(group, theta_ptrs, m_ptrs, v_ptrs, step_ptr: int, lr: float, loss_ptr: int,
+                        y0_ptr: int, steps: int):
+    out = c_void_p()
+    check(load().fbsde_group_capture(group, _ptr_array(theta_ptrs), _ptr_array(m_ptrs), _ptr_array(v_ptrs),
+                                     c_void_p(step_ptr), lr, c_void_p(loss_ptr or None),
+                                     c_void_p(y0_ptr or None), steps, ctypes.byref(out)),
+          "fbsde_group_capture")
+    return out
+
+
+def fbsde_stream_create() -> int:
+    out = c_void_p()
+    check(load().fbsde_stream_create(ctypes.byref(out)), "fbsde_stream_create")
+    return int(out.value)
+
+
+def fbsde_stream_destroy(stream: int):
+    load().fbsde_stream_destroy(c_void_p(stream or None))
+
+
+def fbsde_set_grid_cap(ctx, ctas: int):
+    check(load().fbsde_set_grid_cap(ctx, ctas), "fbsde_set_grid_cap", ctx)
+
+
+def fbsde_group_autotune(group, theta_ptrs, lr: float, trial_steps: int):
+    n = len(theta_ptrs)
+    caps = (c_int * n)()
+    ms = c_float()
+    check(load().fbsde_group_autotune(group, _ptr_array(theta_ptrs), lr, trial_steps, caps, ctypes.byref(ms)),
+          "fbsde_group_autotune")
+    return list(caps), float(ms.value)
 
 
 def fbsde_set_level(ctx, N: int):

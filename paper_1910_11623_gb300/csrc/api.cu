@@ -301,15 +301,6 @@ fbsde_status fbsde_train_step_dev(fbsde_ctx* ctx, float* theta_dev, float* adam_
     return launch_step_advance(ctx, step_dev);
 }
 
-}  // extern "C"
-
-struct fbsde_graph {
-    fbsde_ctx* ctx = nullptr;
-    cudaGraph_t graph = nullptr;
-    cudaGraphExec_t exec = nullptr;
-};
-
-extern "C" {
 
 fbsde_status fbsde_graph_capture(fbsde_ctx* ctx, float* theta_dev, float* adam_m_dev, float* adam_v_dev,
                                  uint64_t* step_dev, float lr, float* loss_dev, float* y0_dev, int steps,
@@ -349,14 +340,14 @@ fbsde_status fbsde_graph_capture(fbsde_ctx* ctx, float* theta_dev, float* adam_m
         cudaGraphDestroy(graph);
         return set_err(ctx, FBSDE_ERR_OOM, "host allocation failed");
     }
-    g->ctx = ctx; g->graph = graph; g->exec = exec;
+    g->ctx = ctx; g->stream = ctx->stream; g->graph = graph; g->exec = exec;
     *out = g;
     return FBSDE_OK;
 }
 
 fbsde_status fbsde_graph_launch(fbsde_graph* graph) {
     if (!graph) return FBSDE_ERR_INVALID;
-    cudaError_t e = cudaGraphLaunch(graph->exec, graph->ctx->stream);
+    cudaError_t e = cudaGraphLaunch(graph->exec, graph->stream);
     if (e != cudaSuccess) return set_err(graph->ctx, FBSDE_ERR_CUDA, std::string("cudaGraphLaunch: ") + cudaGetErrorString(e));
     return FBSDE_OK;
 }

@@ -1029,7 +1029,8 @@ fbsde_status fused_forward(fbsde_ctx* c, const float* theta, bool for_grad) {
     a.off = param_offsets(c);
     a.P = (int)c->P(); a.M = c->M; a.D = c->D; a.Dp = b->Dp; a.Dn = b->Dn; a.w = c->w; a.wp = b->wp;
     a.L = c->L; a.ntiles = (a.P + 127) / 128; a.dt = (float)(c->T / c->N); a.err = b->err;
-    const int grid = a.ntiles < b->grid ? a.ntiles : b->grid;
+    const int cap = c->grid_cap > 0 && c->grid_cap < b->grid ? c->grid_cap : b->grid;
+    const int grid = a.ntiles < cap ? a.ntiles : cap;
     const size_t smem = fwdz_smem_bytes(c->L, c->w);
     const int FT = fused_threads(kFwdGroups);
     const bool res = c->akind == FBSDE_RESNET;
@@ -1089,7 +1090,8 @@ fbsde_status fused_backward(fbsde_ctx* c, const float* theta) {
         if (le != cudaSuccess) return set_err(c, FBSDE_ERR_CUDA, std::string("parameter table: ") + cudaGetErrorString(le));
         ++c->n_launch;
     }
-    const int grid = a.ntiles < b->grid ? a.ntiles : b->grid;
+    const int cap = c->grid_cap > 0 && c->grid_cap < b->grid ? c->grid_cap : b->grid;
+    const int grid = a.ntiles < cap ? a.ntiles : cap;
     const size_t smem = bwd_smem_bytes(c->L, c->w);
     const int FT = bwd_threads(), R = kBwdRegsLaunch;
     const bool res = c->akind == FBSDE_RESNET;

@@ -74,6 +74,10 @@ struct fbsde_ctx {
     // word by the kernels (a step captured in a CUDA graph) instead of being
     // passed by value.
     const uint64_t* step_dev = nullptr;
+    // Upper bound on the CTAs of the fused per-tile kernels (0: one per SM);
+    // set by fbsde_set_grid_cap / the group autotuner so that the instances
+    // of a group share the SMs.
+    int grid_cap = 0;
     fbsde::ParamLayout pl;
     std::string err;
 
@@ -117,6 +121,15 @@ struct fbsde_ctx {
         p.r = (float)r; p.sigma = (float)sigma; p.tgt = tgt;
         return p;
     }
+};
+
+// An instantiated CUDA graph of training steps (fbsde_graph_capture,
+// fbsde_group_capture), replayed on `stream`.
+struct fbsde_graph {
+    fbsde_ctx* ctx = nullptr;  // error reporting (NULL for a group)
+    cudaStream_t stream = nullptr;
+    cudaGraph_t graph = nullptr;
+    cudaGraphExec_t exec = nullptr;
 };
 
 namespace fbsde {

@@ -69,6 +69,10 @@ bool map3d(CUtensorMap* m, const void* base, uint64_t inner, uint64_t outer, uin
 // ------------------------------------------------------------------ workspace
 
 constexpr int kColSplits = 296;
+// Column-sum partials: kColSplits rows of (width + 32) floats, twice (the
+// weight-gradient contractions also keep a t-weighted set; their splits times
+// output rows never exceed kColSplits x width).
+static size_t colpart_floats(int w) { return (size_t)2 * kColSplits * (rup(w, 16) + 16); }
 
 int* bf16_error_flag(fbsde_ctx* c) { return c->bf ? c->bf->err : nullptr; }
 
@@ -106,7 +110,7 @@ fbsde_status bf16_create(fbsde_ctx* c) {
         add((size_t)w * b->wp * 2); add((size_t)w * b->wp * 2);
         add((size_t)w * b->Dp * 2); add((size_t)b->Dn * b->wp * 2);
     }
-    add((size_t)kColSplits * (rup(w, 16) + 16) * sizeof(float));
+    add(colpart_floats(w) * sizeof(float));
     add(256);
     if (b->fused) {
         add((size_t)(L > 0 ? L : 1) * b->G_stride * sizeof(bf16));
@@ -145,7 +149,7 @@ fbsde_status bf16_create(fbsde_ctx* c) {
         b->W[l] = (bf16*)take((size_t)w * b->wp * 2); b->WT[l] = (bf16*)take((size_t)w * b->wp * 2);
         b->Bx[l] = (bf16*)take((size_t)w * b->Dp * 2); b->BxT[l] = (bf16*)take((size_t)b->Dn * b->wp * 2);
     }
-    b->colpart = (float*)take((size_t)kColSplits * (rup(w, 16) + 16) * sizeof(float));
+    b->colpart = (float*)take(colpart_floats(w) * sizeof(float));
     b->err = (int*)take(256);
     if (b->fused) {
         b->G = (bf16*)take((size_t)(L > 0 ? L : 1) * b->G_stride * sizeof(bf16));
@@ -562,7 +566,7 @@ static fbsde_status wgrad(fbsde_ctx* c, TcArgs a, int ncols_store, float* out, i
     }
     a.kchunk = (int)kc;
     Bf16Work* b = c->bf;
-    const size_t cs_cap = (size_t)kColSplits * (rup(c->w, 16) + 16);
+    const size_t cs_cap = colpart_floats(c->w);
     const bool cs = cs_out && (size_t)splits * a.rows * (cst_out ? 2 : 1) <= cs_cap;
     if (cs) {
         a.cs_part = b->colpart;

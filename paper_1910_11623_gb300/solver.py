@@ -232,6 +232,90 @@ class TrainGraph:
             pass
 
 
+class Group:
+    """Independent instances (each a Solver on its own stream) trained
+    together: one group step runs every instance's training step
+    concurrently, capture() makes it one CUDA graph, autotune() splits the
+    SMs between the instances (cached per set of shapes in a JSON file)."""
+
+    def __init__(self, solvers, stream: Optional[torch.cuda.Stream] = None):
+        self.solvers = list(solvers)
+        self.stream = stream or torch.cuda.Stream()
+        self.handle = L.fbsde_group_create([s.ctx for s in self.solvers], self.stream.cuda_stream)
+        n = len(self.solvers)
+        self.loss = torch.empty(n, device="cuda")
+        self.y0 = torch.empty(n, device="cuda")
+
+    def _ptrs(self, ts):
+        return [t.data_ptr() for t in ts]
+
+    def train_step(self, thetas, ms, vs, step_dev, lr: float = 1e-3):
+        L.fbsde_group_train_step(self.handle, self._ptrs(thetas), self._ptrs(ms), self._ptrs(vs),
+                                 step_dev.data_ptr(), lr, self.loss.data_ptr(), self.y0.data_ptr())
+        return self.loss, self.y0
+
+    def capture(self, thetas, ms, vs, step_dev, lr: float = 1e-3, steps: int = 1):
+        g = L.fbsde_group_capture(self.handle, self._ptrs(thetas), self._ptrs(ms), self._ptrs(vs),
+                                  step_dev.data_ptr(), lr, self.loss.data_ptr(), self.y0.data_ptr(), steps)
+        return _GraphHandle(g, (thetas, ms, vs, step_dev))
+
+    def shapes_key(self) -> str:
+        import json
+        return json.dumps([[s.problem.kind, s.problem.D, s.problem_N, s.problem.M, s.arch.kind, s.arch.width,
+                            s.arch.depth, s.arch.act, s.arch.prec] for s in self.solvers])
+
+    def autotune(self, thetas, lr: float = 1e-3, trial_steps: int = 2, cache_path: Optional[str] = None):
+        """Per-instance caps on the fused kernels' CTAs; read from / written
+        to cache_path keyed by the instances' shapes."""
+        import json, os
+        key = self.shapes_key()
+        cache = {}
+        if cache_path and os.path.exists(cache_path):
+            with open(cache_path) as f:
+                cache = json.load(f)
+        if key in cache:
+            caps = cache[key]["caps"]
+            for s, c in zip(self.solvers, caps):
+                L.fbsde_set_grid_cap(s.ctx, int(c))
+            return caps, cache[key].get("ms_per_step"), True
+        caps, ms = L.fbsde_group_autotune(self.handle, self._ptrs(thetas), lr, trial_steps)
+        if cache_path:
+            cache[key] = {"caps": caps, "ms_per_step": ms}
+            with open(cache_path, "w") as f:
+                json.dump(cache, f)
+        return caps, ms, False
+
+    def close(self):
+        if self.handle:
+            L.fbsde_group_destroy(self.handle)
+            self.handle = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+
+class _GraphHandle:
+    def __init__(self, handle, keep):
+        self.handle, self._keep = handle, keep
+
+    def launch(self):
+        L.fbsde_graph_launch(self.handle)
+
+    def close(self):
+        if self.handle:
+            L.fbsde_graph_destroy(self.handle)
+            self.handle = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+
 def philox4x32_10(ctr: torch.Tensor, key0: int, key1: int) -> torch.Tensor:
     """Raw Philox4x32-10 blocks on the GPU: ctr int32 [n, 4] (bit patterns) -> [n, 4]."""
     assert ctr.is_cuda and ctr.dtype == torch.int32 and ctr.is_contiguous() and ctr.shape[-1] == 4

@@ -70,3 +70,38 @@ def bsb_y0(x0, r: float = 0.05, sigma: float = 0.4, T: float = 1.0) -> float:
 MULTILEVEL_LEVELS = (4, 8, 16, 32, 64)
 MULTILEVEL_COARSE_STEPS = 100
 
+
+def batched_instances(seed: int = 0, n: int = 32, budget_gb: float = 140.0):
+    """Uneven independent instances (half BSB, half HJB): D from
+    {10, 20, 50, 100, 200}, N from {16, 32, 64, 128}, M from {1024, 4096,
+    16384}, ResNet 4 x w tanh with w from {128, 256}, all seeded.  The
+    largest instances' M is halved until the estimated device memory of all
+    workspaces fits `budget_gb`.  Returns a list of Workloads."""
+    import random
+    rng = random.Random(seed)
+    specs = []
+    for i in range(n):
+        kind = "bsb" if i % 2 == 0 else "hjb"
+        D = rng.choice([10, 20, 50, 100, 200])
+        N = rng.choice([16, 32, 64, 128])
+        M = rng.choice([1024, 4096, 16384])
+        w = rng.choice([128, 256])
+        specs.append([kind, D, N, M, w])
+
+    def est_bytes(D, N, M, w, L=4):
+        P = M * (N + 1)
+        Dp = (D + 63) // 64 * 64
+        per_point = 4 * (L + 1) * 2 * w + L * 2 * w + 2 * 2 * Dp + 4 * 4 * D + 64
+        return P * per_point + 152 * (2 * L + 2) * 128 * w * 2
+
+    while sum(est_bytes(D, N, M, w) for _, D, N, M, w in specs) > budget_gb * 1e9:
+        big = max(range(n), key=lambda i: est_bytes(*specs[i][1:]))
+        specs[big][3] //= 2
+    out = []
+    for i, (kind, D, N, M, w) in enumerate(specs):
+        x0 = bsb_x0(D) if kind == "bsb" else [0.0] * D
+        out.append(Workload(f"inst{i}_{kind}_d{D}_n{N}_m{M}_resnet4x{w}",
+                            ProblemSpec(kind=kind, D=D, N=N, M=M, x0=x0),
+                            ArchSpec(kind="resnet", width=w, depth=4, act="tanh", prec="bf16"), seed=seed + i))
+    return out
+

@@ -121,3 +121,12 @@ def test_graph_entry_points_reject_null_arguments_without_a_gpu(L):
     assert lib.fbsde_graph_launch(None) == L.FBSDE_ERR_INVALID
     assert lib.fbsde_graph_destroy(None) == L.FBSDE_OK
     assert lib.fbsde_train_step_dev(None, None, None, None, None, 1e-3, None, None) == L.FBSDE_ERR_INVALID
+
+
+def test_group_entry_points_reject_bad_arguments_without_a_gpu(L):
+    lib = L.load()
+    out = L.c_void_p()
+    assert lib.fbsde_group_create(None, 0, None, L.ctypes.byref(out)) == L.FBSDE_ERR_INVALID
+    assert lib.fbsde_group_destroy(None) == L.FBSDE_OK
+    assert lib.fbsde_group_train_step(None, None, None, None, None, 1e-3, None, None) == L.FBSDE_ERR_INVALID
+    assert lib.fbsde_set_grid_cap(None, 0) == L.FBSDE_ERR_INVALID

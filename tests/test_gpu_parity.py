@@ -309,3 +309,53 @@ def test_graph_replay_is_the_same_training(P, prec):
     assert rel_max(th_b.cpu().numpy().astype(np.float64), tho) < TOL[prec]
     g.close()
     s.close()
+
+
+def test_group_of_uneven_instances(P, tmp_path):
+    # instances of different problems and shapes trained together (one
+    # forked group step, its graph, the autotuned SM split) give exactly what
+    # each instance gives trained alone
+    specs = [
+        (P.ProblemSpec(kind="bsb", D=6, N=4, M=32, x0=[1.0, 0.5] * 3),
+         P.ArchSpec(kind="resnet", width=32, depth=2, act="tanh", prec="bf16")),
+        (P.ProblemSpec(kind="hjb", D=13, N=7, M=37, x0=[0.0] * 13),
+         P.ArchSpec(kind="fc", width=48, depth=3, act="sin", prec="bf16")),
+        (P.ProblemSpec(kind="bsb", D=4, N=8, M=16, x0=[1.0] * 4),
+         P.ArchSpec(kind="resnet", width=16, depth=1, act="tanh", prec="fp32")),
+    ]
+    solo, grouped = [], []
+    for k, (prob, arch) in enumerate(specs):
+        s = P.Solver(prob, arch, seed=10 + k, stream=torch.cuda.Stream())
+        th = s.init_params()
+        solo.append((s, th.clone(), torch.zeros_like(th), torch.zeros_like(th)))
+        s2 = P.Solver(prob, arch, seed=10 + k, stream=torch.cuda.Stream())
+        grouped.append((s2, th.clone(), torch.zeros_like(th), torch.zeros_like(th)))
+    for s, th, m, v in solo:
+        with torch.cuda.stream(s.stream):
+            for step in range(1, 4):
+                s.train_step(th, m, v, step, 1e-3)
+        s.stream.synchronize()
+    G = P.Group([g[0] for g in grouped])
+    ths, ms, vs = [g[1] for g in grouped], [g[2] for g in grouped], [g[3] for g in grouped]
+    caps, ms_step, cached = G.autotune(ths, trial_steps=1, cache_path=str(tmp_path / "tune.json"))
+    assert len(caps) == 3 and not cached
+    assert G.autotune(ths, cache_path=str(tmp_path / "tune.json"))[2]  # second call: from the cache
+    step_dev = torch.ones(3, dtype=torch.int64, device="cuda")
+    with torch.cuda.stream(G.stream):
+        G.train_step(ths, ms, vs, step_dev, 1e-3)
+        graph = G.capture(ths, ms, vs, step_dev, 1e-3, steps=2)
+        graph.launch()
+    G.stream.synchronize()
+    assert step_dev.tolist() == [4, 4, 4]
+    for (s, th, m, v), (_, thg, mg, vg) in zip(solo, grouped):
+        assert torch.equal(th, thg) and torch.equal(m, mg) and torch.equal(v, vg)
+    graph.close()
+    G.close()
+
+
+def test_bf16_many_point_splits_width128(P):
+    # enough points that the weight-gradient contraction splits K into its
+    # full number of chunks at width 128 (column sums of every split kept)
+    prob = P.ProblemSpec(kind="hjb", D=20, N=40, M=512, x0=[0.0] * 20)
+    arch = P.ArchSpec(kind="resnet", width=128, depth=2, act="tanh", prec="bf16")
+    _check_eval(P, prob, arch, seed=8, it=3, perturb=0.05)
