@@ -158,6 +158,7 @@ fbsde_status fbsde_create(const fbsde_problem* problem, const fbsde_arch* arch, 
     add((c->N_max + 1) * (size_t)c->M * D);  // X
     add((size_t)c->N_max * c->M * D);        // dW
     add(Pm); add(Pm * D); add(Pm); add(Pm * D); add(2 * Pm);  // Y Z alpha V ones_t
+    add(Pm);                   // residuals r_n
     add(2 * (size_t)c->M);     // path_loss (double)
     if (c->akind == FBSDE_NAIS) { add(2 * L * w * w); }
     add(w * w);                // sym
@@ -182,6 +183,7 @@ fbsde_status fbsde_create(const fbsde_problem* problem, const fbsde_arch* arch, 
     c->dW = take((size_t)c->N_max * c->M * D);
     c->Y = take(Pm); c->Z = take(Pm * D); c->alpha = take(Pm); c->V = take(Pm * D);
     c->ones_t = take(2 * Pm);
+    c->rbuf = take(Pm);
     c->path_loss_d = (double*)take(2 * (size_t)c->M);
     if (c->akind == FBSDE_NAIS)
         for (int l = 1; l <= c->L; ++l) { c->Amat[l] = take(w * w); c->gA[l] = take(w * w); }

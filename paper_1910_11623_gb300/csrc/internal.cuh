@@ -93,6 +93,8 @@ struct fbsde_ctx {
     float* V = nullptr;        // d loss / d Z_n       [(N_max+1) M, D]
     float* ones_t = nullptr;   // (1, t_n) per point   [(N_max+1) M, 2]
     double* path_loss_d = nullptr;  // per-path loss   [M]
+    float* rbuf = nullptr;     // Y-residuals r_n      [N_max M]
+    bool need_V32 = true;      // FP32 v_n consumed (FP32 form, layered BF16 sweeps)
     float* Amat[fbsde::kMaxDepth + 1] = {};  // NAIS A_l = -R^T R - eps I [w, w]
     float* gA[fbsde::kMaxDepth + 1] = {};    // NAIS d loss / d A_l       [w, w]
     float* sym = nullptr;      // NAIS scratch [w, w]

@@ -16,6 +16,8 @@ namespace fbsde {
 // One thread per (path m, dimension quad q): walks the N steps of its path,
 // drawing Delta W_n from Philox counter (q, n, m, iter) and updating
 // X_{n+1} = X_n + sigma(X_n) Delta W_n.  Layout: row n * M + m, column d.
+// With D a multiple of 4 a quad's row pieces are written as single 16-byte
+// (FP32) and 8-byte (BF16) stores.
 __global__ void k_paths(ProblemDev pd, const float* __restrict__ x0, uint32_t k0, uint32_t k1,
                         uint32_t it_host, const uint64_t* __restrict__ it_dev, float* __restrict__ X,
                         float* __restrict__ dW, __nv_bfloat16* __restrict__ Xb, int ldb) {
@@ -26,17 +28,28 @@ __global__ void k_paths(ProblemDev pd, const float* __restrict__ x0, uint32_t k0
     const int m = (int)(idx / Q), q = (int)(idx % Q);
     const int d0 = 4 * q;
     const int nd = min(4, pd.D - d0);
+    const bool vec = (pd.D & 3) == 0 && (ldb & 3) == 0;
     float x[4];
 #pragma unroll
     for (int j = 0; j < 4; ++j) x[j] = (j < nd) ? x0[d0 + j] : 0.f;
-    if (X) {
-        float* row = X + (size_t)m * pd.D + d0;
-        for (int j = 0; j < nd; ++j) row[j] = x[j];
-    }
-    if (Xb) {
-        __nv_bfloat16* row = Xb + (size_t)m * ldb + d0;
-        for (int j = 0; j < nd; ++j) row[j] = __float2bfloat16_rn(x[j]);
-    }
+    auto put = [&](float* frow, __nv_bfloat16* brow, const float* v) {
+        if (vec) {
+            if (frow) *reinterpret_cast<float4*>(frow) = make_float4(v[0], v[1], v[2], v[3]);
+            if (brow) {
+                __nv_bfloat162 lo = __floats2bfloat162_rn(v[0], v[1]), hi = __floats2bfloat162_rn(v[2], v[3]);
+                uint2 u;
+                u.x = *reinterpret_cast<uint32_t*>(&lo);
+                u.y = *reinterpret_cast<uint32_t*>(&hi);
+                *reinterpret_cast<uint2*>(brow) = u;
+            }
+        } else {
+            if (frow)
+                for (int j = 0; j < nd; ++j) frow[j] = v[j];
+            if (brow)
+                for (int j = 0; j < nd; ++j) brow[j] = __float2bfloat16_rn(v[j]);
+        }
+    };
+    put(X ? X + (size_t)m * pd.D + d0 : nullptr, Xb ? Xb + (size_t)m * ldb + d0 : nullptr, x);
     const float sqrt2 = 1.41421356237309515f;
     for (int n = 0; n < pd.N; ++n) {
         u32x4 c{(uint32_t)q, (uint32_t)n, (uint32_t)m, it};
@@ -51,18 +64,9 @@ __global__ void k_paths(ProblemDev pd, const float* __restrict__ x0, uint32_t k0
             if (pd.kind == FBSDE_BSB) x[j] = x[j] + (pd.sigma * x[j]) * dw[j];
             else                      x[j] = x[j] + sqrt2 * dw[j];
         }
-        if (dW) {
-            float* row = dW + ((size_t)n * pd.M + m) * pd.D + d0;
-            for (int j = 0; j < nd; ++j) row[j] = dw[j];
-        }
-        if (X) {
-            float* row = X + ((size_t)(n + 1) * pd.M + m) * pd.D + d0;
-            for (int j = 0; j < nd; ++j) row[j] = x[j];
-        }
-        if (Xb) {
-            __nv_bfloat16* row = Xb + ((size_t)(n + 1) * pd.M + m) * ldb + d0;
-            for (int j = 0; j < nd; ++j) row[j] = __float2bfloat16_rn(x[j]);
-        }
+        put(dW ? dW + ((size_t)n * pd.M + m) * pd.D + d0 : nullptr, nullptr, dw);
+        put(X ? X + ((size_t)(n + 1) * pd.M + m) * pd.D + d0 : nullptr,
+            Xb ? Xb + ((size_t)(n + 1) * pd.M + m) * ldb + d0 : nullptr, x);
     }
 }
 
@@ -256,12 +260,108 @@ fbsde_status copy_path_loss(fbsde_ctx* ctx, float* out) {
     return FBSDE_OK;
 }
 
+// The same residuals and seeds as k_seeds, parallel over the points: one warp
+// per point (n, m), n < N, forms r_n (Eq. "loss") and v_n, and stores r_n;
+// k_seeds_paths then forms alpha_n from r_{n-1} and r_n, the per-path loss
+// (FP64, fixed order) and the terminal point.
+__global__ void k_resid(ProblemDev pd, const float* __restrict__ X, const float* __restrict__ dW,
+                        const float* __restrict__ Y, const float* __restrict__ Z, float* __restrict__ rbuf,
+                        float* __restrict__ V, __nv_bfloat16* __restrict__ Vb, int ldb) {
+    const int lane = threadIdx.x & 31;
+    const long wp = ((long)blockIdx.x * blockDim.x + threadIdx.x) >> 5;
+    if (wp >= (long)pd.N * pd.M) return;
+    const size_t p = (size_t)wp;  // n * M + m
+    const int D = pd.D;
+    const bool bsb = pd.kind == FBSDE_BSB;
+    const float sqrt2 = 1.41421356237309515f;
+    const float* x = X + p * D;
+    const float* z = Z + p * D;
+    const float* dw = dW + p * D;
+    float zx = 0.f, zsdw = 0.f, zz = 0.f;
+    for (int d = lane; d < D; d += 32) {
+        const float xd = x[d], zd = z[d];
+        const float sdw = bsb ? pd.sigma * xd * dw[d] : sqrt2 * dw[d];
+        zx = fmaf(zd, xd, zx);
+        zsdw = fmaf(zd, sdw, zsdw);
+        zz = fmaf(zd, zd, zz);
+    }
+    zx = warp_sum(zx); zsdw = warp_sum(zsdw); zz = warp_sum(zz);
+    const float yn = Y[p], yn1 = Y[p + pd.M];
+    const float phi = bsb ? pd.r * (yn - zx) : zz;
+    const float r = yn1 - yn - phi * pd.dt - zsdw;
+    if (lane == 0) rbuf[p] = r;
+    for (int d = lane; d < D; d += 32) {
+        const float sdw = bsb ? pd.sigma * x[d] * dw[d] : sqrt2 * dw[d];
+        const float phiz = bsb ? -pd.r * x[d] : 2.f * z[d];
+        const float v = -2.f * r * (phiz * pd.dt + sdw);
+        if (V) V[p * D + d] = v;
+        if (Vb) Vb[p * ldb + d] = __float2bfloat16_rn(v);
+    }
+}
+
+__global__ void k_seeds_paths(ProblemDev pd, const float* __restrict__ X, const float* __restrict__ Y,
+                              const float* __restrict__ Z, const float* __restrict__ rbuf,
+                              float* __restrict__ alpha, float* __restrict__ V, double* __restrict__ path_loss,
+                              __nv_bfloat16* __restrict__ Vb, int ldb) {
+    const int lane = threadIdx.x & 31;
+    const int m = (int)(((long)blockIdx.x * blockDim.x + threadIdx.x) >> 5);
+    if (m >= pd.M) return;
+    const int D = pd.D;
+    const bool bsb = pd.kind == FBSDE_BSB;
+    const float phi_y = bsb ? pd.r : 0.f;
+    double pl = 0.0;
+    for (int n = lane; n < pd.N; n += 32) {
+        const size_t p = (size_t)n * pd.M + m;
+        const float r = rbuf[p];
+        pl += (double)r * (double)r;
+        alpha[p] = (n >= 1 ? 2.f * rbuf[p - pd.M] : 0.f) - 2.f * r * (1.f + phi_y * pd.dt);
+    }
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) pl += __shfl_xor_sync(0xffffffffu, pl, o);
+    const float rprev = pd.N >= 1 ? rbuf[(size_t)(pd.N - 1) * pd.M + m] : 0.f;
+    // terminal point n = N
+    const size_t p = (size_t)pd.N * pd.M + m;
+    const float* x = X + p * D;
+    const float* z = Z + p * D;
+    float s = 0.f;
+    for (int d = lane; d < D; d += 32) s = fmaf(x[d], x[d], s);
+    s = warp_sum(s);
+    const float g = bsb ? s : logf(0.5f * (1.f + s));
+    const float rT = Y[p] - g;
+    pl += (double)rT * (double)rT;
+    float zt = 0.f;
+    for (int d = lane; d < D; d += 32) {
+        float v = 0.f;
+        if (pd.tgt) {
+            const float gg = bsb ? 2.f * x[d] : 2.f * x[d] / (1.f + s);
+            const float diff = z[d] - gg;
+            v = 2.f * diff;
+            zt = fmaf(diff, diff, zt);
+        }
+        if (V) V[p * D + d] = v;
+        if (Vb) Vb[p * ldb + d] = __float2bfloat16_rn(v);
+    }
+    zt = warp_sum(zt);
+    if (pd.tgt) pl += (double)zt;
+    if (lane == 0) {
+        alpha[p] = (pd.N >= 1 ? 2.f * rprev : 0.f) + 2.f * rT;
+        path_loss[m] = pl;
+    }
+}
+
 fbsde_status launch_seeds(fbsde_ctx* ctx, float* loss_dev, float* y0_dev) {
     ProblemDev pd = ctx->pdev();
     const int wpb = 8;  // warps per block
     const int tok = prof_begin(ctx, PROF_OTHER);
-    k_seeds<<<(pd.M + wpb - 1) / wpb, 32 * wpb, 0, ctx->stream>>>(
-        pd, ctx->X, ctx->dW, ctx->Y, ctx->Z, ctx->alpha, ctx->V, ctx->path_loss_d, ctx->Vb_op, ctx->ld_op);
+    float* V = ctx->need_V32 ? ctx->V : nullptr;
+    const long pts = (long)pd.N * pd.M;
+    if (pts > 0) {
+        k_resid<<<(unsigned)((pts + wpb - 1) / wpb), 32 * wpb, 0, ctx->stream>>>(
+            pd, ctx->X, ctx->dW, ctx->Y, ctx->Z, ctx->rbuf, V, ctx->Vb_op, ctx->ld_op);
+        FBSDE_CK_LAUNCH(ctx);
+    }
+    k_seeds_paths<<<(pd.M + wpb - 1) / wpb, 32 * wpb, 0, ctx->stream>>>(
+        pd, ctx->X, ctx->Y, ctx->Z, ctx->rbuf, ctx->alpha, V, ctx->path_loss_d, ctx->Vb_op, ctx->ld_op);
     FBSDE_CK_LAUNCH(ctx);
     k_loss_reduce<<<1, 1024, 0, ctx->stream>>>(ctx->path_loss_d, pd.M, ctx->Y, loss_dev, y0_dev,
                                                ctx->nonfinite);

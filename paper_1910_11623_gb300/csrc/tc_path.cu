@@ -89,6 +89,7 @@ fbsde_status bf16_create(fbsde_ctx* c) {
     const size_t nl = (size_t)L + 1;
     // per-tile fused kernels: FC / ResNet, depth <= kFusedMaxDepth, D <= 256
     b->fused = c->akind != FBSDE_NAIS && L <= kFusedMaxDepth && b->Dp <= 256;
+    c->need_V32 = !b->fused;  // the fused backward reads the BF16 v rows only
     if (b->fused) {
         int dev = 0, sms = 0;
         FBSDE_CK(c, cudaGetDevice(&dev));
