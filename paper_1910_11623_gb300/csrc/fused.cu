@@ -526,17 +526,27 @@ __global__ void __launch_bounds__(fused_threads(kFwdGroups), 1) k_fused_fwdz(con
         const int nch = a.w / 8;
         int qg = 0, tcount = 0;
         bool ok = true;
+        // network input (t enters as a per-row bias): the BF16 X rows by TMA,
+        // requested for the next tile as soon as the Z contraction has read
+        // the current one, so that the load overlaps the Z epilogue
+        auto request_x = [&](int tile_index) {
+            if (ss.st_thread) {
+                tc::mbar_expect_tx(xfull, (uint32_t)(a.Dp / 64) * 16384u);
+                for (int k = 0; k < a.Dp / 64; ++k)
+                    tc::tma_load_2d(tile + k * 16384, &a.xin, xfull, k * 64, tile_index * 128);
+            }
+        };
+        bool requested = false;
         for (int t = blockIdx.x; t < a.ntiles && ok; t += gridDim.x) {
             const int p = t * 128 + row;
             const bool valid = p < a.P;
             const float tval = valid ? (float)(p / a.M) * a.dt : 0.f;
             uint32_t* gtile = a.G + (size_t)t * blk;
-            // network input (t enters as a per-row bias): the BF16 X rows by TMA
-            if (!ss.before_write()) { ok = false; break; }
-            if (ss.st_thread) {
-                tc::mbar_expect_tx(xfull, (uint32_t)(a.Dp / 64) * 16384u);
-                for (int k = 0; k < a.Dp / 64; ++k) tc::tma_load_2d(tile + k * 16384, &a.xin, xfull, k * 64, t * 128);
+            if (!requested) {
+                if (!ss.before_write()) { ok = false; break; }
+                request_x(t);
             }
+            requested = false;
             if (!tc::mbar_wait(xfull, (uint32_t)tcount & 1u, tc::kWaitBudget)) { ok = false; break; }
             ++tcount;
             if (!ss.after_write(aready)) { ok = false; break; }
@@ -548,6 +558,11 @@ __global__ void __launch_bounds__(fused_threads(kFwdGroups), 1) k_fused_fwdz(con
                 tc::tc_fence_after();
                 const bool writes_tile = q <= 2 * L;
                 if (writes_tile && !ss.before_write()) { ok = false; break; }
+                if (q == nq - 1 && t + (int)gridDim.x < a.ntiles) {
+                    if (!ss.before_write()) { ok = false; break; }
+                    request_x(t + (int)gridDim.x);
+                    requested = true;
+                }
                 int store_layer = -1;  // e_l stored from the tile after this phase
                 if (q <= L) {
                     // forward layer l: a = acc + b_l (+ t W_in[:,0]); h_l = [h_{l-1}] + act(a)
@@ -632,9 +647,19 @@ __global__ void __launch_bounds__(fused_threads(kFwdGroups), 1) k_fused_fwdz(con
                         tc::tmem_ld8(tacc + (uint32_t)c0, rv);
                         tc::tmem_wait_ld();
                         if (valid) {
+                            float* zr = a.Z + (size_t)p * a.D + c0;
+                            if ((a.D & 3) == 0 && c0 + 8 <= a.D) {
+                                reinterpret_cast<float4*>(zr)[0] = make_float4(
+                                    __uint_as_float(rv[0]), __uint_as_float(rv[1]), __uint_as_float(rv[2]),
+                                    __uint_as_float(rv[3]));
+                                reinterpret_cast<float4*>(zr)[1] = make_float4(
+                                    __uint_as_float(rv[4]), __uint_as_float(rv[5]), __uint_as_float(rv[6]),
+                                    __uint_as_float(rv[7]));
+                            } else {
 #pragma unroll
-                            for (int j = 0; j < 8; ++j)
-                                if (c0 + j < a.D) a.Z[(size_t)p * a.D + c0 + j] = __uint_as_float(rv[j]);
+                                for (int j = 0; j < 8; ++j)
+                                    if (c0 + j < a.D) zr[j] = __uint_as_float(rv[j]);
+                            }
                         }
                     }
                 }
@@ -815,6 +840,7 @@ __global__ void __launch_bounds__(bwd_threads(), 1) k_fused_bwd(const __grid_con
         const int nch = a.w / 8;
         const int nkw = a.wp / 64, nkx = a.Dp / 64;
         int qg = 0, tcount = 0;
+        bool v_requested = false;
         bool ok = true;
         // A wait that runs out of budget clears `ok` but the thread still
         // goes through the phase (the named barriers of the slab stores need
@@ -826,15 +852,18 @@ __global__ void __launch_bounds__(bwd_threads(), 1) k_fused_bwd(const __grid_con
             const float tval = valid ? (float)(p / a.M) * a.dt : 0.f;
             const float alpha_p = valid ? __ldg(a.alpha + p) : 0.f;
             const uint32_t* gtile = a.G + (size_t)t * blk;
-            // inputs: (t, X) for the forward, (0, v) for the tangent, BF16 rows by TMA
+            // inputs: (t, X) for the forward, (0, v) for the tangent, BF16 rows
+            // by TMA; the v rows were requested during the previous tile's
+            // adjoint sweep (tile_d is free once the up-sweep is done)
             if (ok) ok = ss.before_write();
             if (ss.st_thread) {
-                tc::mbar_expect_tx(xfull, (uint32_t)nkx * 2u * 16384u);
+                tc::mbar_expect_tx(xfull, (uint32_t)nkx * (v_requested ? 1u : 2u) * 16384u);
                 for (int k = 0; k < nkx; ++k) {
                     tc::tma_load_2d(tile_h + k * 16384, &a.xb, xfull, k * 64, t * 128);
-                    tc::tma_load_2d(tile_d + k * 16384, &a.vb, xfull, k * 64, t * 128);
+                    if (!v_requested) tc::tma_load_2d(tile_d + k * 16384, &a.vb, xfull, k * 64, t * 128);
                 }
             }
+            v_requested = false;
             if (ok) ok = tc::mbar_wait(xfull, (uint32_t)tcount & 1u, tc::kWaitBudget);
             ++tcount;
             if (ok) ok = ss.after_write(aready);
@@ -842,6 +871,16 @@ __global__ void __launch_bounds__(bwd_threads(), 1) k_fused_bwd(const __grid_con
                 if (ok) ok = tc::mbar_wait(accf, (uint32_t)qg & 1u, tc::kWaitBudget);
                 tc::tc_fence_after();
                 if (ok) ok = ss.before_write();
+                if (q == L + 1 && t + (int)gridDim.x < a.ntiles) {
+                    // the last reader of tile_d was the dual contraction of
+                    // layer L and its stores have drained (before_write)
+                    if (ss.st_thread) {
+                        tc::mbar_expect_tx_only(xfull, (uint32_t)nkx * 16384u);
+                        for (int k = 0; k < nkx; ++k)
+                            tc::tma_load_2d(tile_d + k * 16384, &a.vb, xfull, k * 64, (t + (int)gridDim.x) * 128);
+                    }
+                    v_requested = true;
+                }
                 if (q <= L) {
                     // layer l forward and tangent:
                     //   a = acc + b (+ t W_in[:,0]),  h_l = [h_{l-1}] + act(a)
