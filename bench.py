@@ -51,6 +51,8 @@ def parse_args():
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--loss-steps", type=int, default=20,
                     help="timed loss-only evaluations (forward sweep + residuals), 0: skip")
+    ap.add_argument("--fp8-steps", type=int, default=1000,
+                    help="Adam steps of the FP8-hidden-layer form (timed for speed, then trained; 0: skip)")
     ap.add_argument("--batched-steps", type=int, default=3,
                     help="timed group steps of the 32 uneven instances (0: skip)")
     ap.add_argument("--M", type=int, default=0,
@@ -497,6 +499,35 @@ def main():
             out["fp32_form"] = {"value": v32rate, "unit": "it/s", "steps": args.fp32_steps}
             out["speedup_vs_fp32_form"] = value / v32rate
         del s32
+        torch.cuda.empty_cache()
+
+    # FP8 hidden layers (E4M3 forward contractions of layers 1..L): speed and
+    # the Y0 reached after a bounded training run
+    if args.form == "bf16" and args.fp8_steps > 0:
+        try:
+            w8 = w.with_prec("fp8")
+            s8 = P.Solver(w8.problem, w8.arch, seed=w.seed + rank, stream=torch.cuda.Stream())
+            th8 = s8.init_params()
+            m8, v8 = torch.zeros_like(th8), torch.zeros_like(th8)
+            with torch.cuda.stream(s8.stream):
+                for s in range(1, 4):
+                    s8.train_step(th8, m8, v8, s, w.lr)
+            ms8 = time_steps(s8, th8, m8, v8, 4, args.fp32_steps or 10, w.lr)
+            res8 = {"value": (args.fp32_steps or 10) / (ms8 / 1000.0), "unit": "it/s"}
+            if w.problem.kind == "bsb" and w.problem.D == 100:
+                target = P.workloads.BSB_Y0_D100
+                with torch.cuda.stream(s8.stream):
+                    for s in range(4 + (args.fp32_steps or 10), args.fp8_steps + 1):
+                        _, y08 = s8.train_step(th8, m8, v8, s, w.lr)
+                s8.stream.synchronize()
+                res8.update({"train_steps": args.fp8_steps, "y0": y08.item(),
+                             "y0_rel_err": abs(y08.item() - target) / target})
+            if out is not None:
+                out["fp8_hidden_form"] = res8
+            s8.close()
+        except Exception as exc:
+            if out is not None:
+                out["fp8_hidden_form"] = {"error": f"{type(exc).__name__}: {exc}"}
         torch.cuda.empty_cache()
 
     # accuracy: train from Theta_0 and track |Y0 - closed form| / closed form

@@ -81,7 +81,14 @@ typedef enum { FBSDE_SIN = 0, FBSDE_TANH = 1 } fbsde_act;
 /* Arithmetic of the network GEMMs.  FBSDE_FP32: CUDA-core FP32 throughout.
  * FBSDE_BF16: BF16 operands on the tcgen05 tensor cores with FP32
  * accumulation; X, Y, residuals, reductions and Adam stay FP32. */
-typedef enum { FBSDE_FP32 = 0, FBSDE_BF16 = 1 } fbsde_prec;
+/* Arithmetic forms.  FBSDE_FP8_HIDDEN: the BF16 form with the forward
+ * contractions of the hidden layers (W_l h_{l-1}, l = 1..L, in the rollout
+ * that gives Y, Z and the loss) in FP8 E4M3 with per-tensor scales and FP32
+ * accumulation; the lift, the Z pass, the gradient sweeps and the weight
+ * gradients stay BF16.  Needs an FC or ResNet network served by the fused
+ * kernels (depth <= 8, width <= 256 and a multiple of 32, D <= 255), else
+ * FBSDE_ERR_UNSUPPORTED at create. */
+typedef enum { FBSDE_FP32 = 0, FBSDE_BF16 = 1, FBSDE_FP8_HIDDEN = 2 } fbsde_prec;
 
 /* Problem specification (Section 2.1 Eq. "coupled" with mu = 0, Section 4). */
 typedef struct {

@@ -18,7 +18,7 @@ FBSDE_ERR_NONFINITE, FBSDE_ERR_TIMEOUT, FBSDE_ERR_OOM = 4, 5, 6
 FBSDE_BSB, FBSDE_HJB = 0, 1
 FBSDE_FC, FBSDE_RESNET, FBSDE_NAIS = 0, 1, 2
 FBSDE_SIN, FBSDE_TANH = 0, 1
-FBSDE_FP32, FBSDE_BF16 = 0, 1
+FBSDE_FP32, FBSDE_BF16, FBSDE_FP8_HIDDEN = 0, 1, 2
 
 
 class fbsde_problem(ctypes.Structure):

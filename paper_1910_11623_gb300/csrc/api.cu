@@ -86,7 +86,8 @@ static std::string validate(const fbsde_problem* pb, const fbsde_arch* ar, int N
         if (!(ar->eps > 0) || !std::isfinite(ar->eps)) return "arch.eps must be finite and > 0 for NAIS";
         if (!std::isfinite(ar->proj_delta)) return "arch.proj_delta must be finite";
     }
-    if (ar->prec != FBSDE_FP32 && ar->prec != FBSDE_BF16) return "arch.prec must be FBSDE_FP32 or FBSDE_BF16";
+    if (ar->prec != FBSDE_FP32 && ar->prec != FBSDE_BF16 && ar->prec != FBSDE_FP8_HIDDEN)
+        return "arch.prec must be FBSDE_FP32, FBSDE_BF16 or FBSDE_FP8_HIDDEN";
     if (N_max != 0 && N_max < pb->N) return "N_max must be 0 or >= problem.N";
     const long long nm = N_max ? N_max : pb->N;
     if ((long long)pb->M * (nm + 1) >= (1LL << 31)) return "M * (N_max + 1) must be < 2^31";
@@ -204,7 +205,7 @@ fbsde_status fbsde_create(const fbsde_problem* problem, const fbsde_arch* arch, 
         delete c;
         return fail(FBSDE_ERR_CUDA, std::string("workspace setup: ") + cudaGetErrorString(e));
     }
-    if (c->prec == FBSDE_BF16) {
+    if (c->prec != FBSDE_FP32) {
         fbsde_status s = bf16_create(c);
         if (s != FBSDE_OK) {
             std::string m = c->err;

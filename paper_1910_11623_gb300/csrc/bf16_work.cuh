@@ -78,7 +78,25 @@ struct Bf16Work {
     size_t G_stride = 0;   // elements between consecutive g_l
     bf16* scratch = nullptr;  // per-CTA activation-derivative scratch
     float* pvec = nullptr;    // [(L+3) x w] per-column parameters of the fused backward
+    // FP8 hidden layers (prec FBSDE_FP8_HIDDEN): E4M3 copies of W_l (l >= 1),
+    // [w x wp8] bytes, their maps (box {128, w}) and per-layer inverse scales
+    bool f8 = false;
+    int wp8 = 0;
+    uint8_t* W8[kMaxDepth + 1] = {};
+    CUtensorMap mW8[kMaxDepth + 1];
+    float* f8inv = nullptr;  // [L + 1]: 1 / (scale of h_{l-1} x scale of W_l)
 };
+
+// Scale of the E4M3 copy of h_l (the operand of layer l + 1): the largest
+// power of two s with s x bound(h_l) <= 448, the largest finite E4M3 value;
+// bound = l + 1 for a ResNet (h_0 = act(.) in [-1, 1], each block adds at
+// most 1), 1 for an FC network (|act| <= 1 for tanh and sin).
+__host__ __device__ inline float e4m3_act_scale(int l, bool res) {
+    const float bound = res ? (float)(l + 1) : 1.f;
+    float s = 1.f;
+    while (bound * s * 2.f <= 448.f) s *= 2.f;
+    return s;
+}
 
 
 fbsde_status fused_forward(fbsde_ctx* c, const float* theta, bool for_grad);

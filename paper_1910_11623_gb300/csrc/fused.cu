@@ -29,6 +29,7 @@
 // of the weight-gradient contractions: h_l, h'_l, e_l, abar_l (BF16).
 #include <cuda.h>
 #include <cuda_bf16.h>
+#include <cuda_fp8.h>
 #include <cuda_runtime.h>
 
 #include <cstring>
@@ -73,6 +74,7 @@ struct FGemm {
     int dual;            // 1: also multiply tile 1 by the same weights into TMEM columns 256..
     int dcol = 0;        // TMEM column of the accumulator
     int acc = 0;         // 1: add to the accumulator's contents (a residual kept there)
+    int f8 = 0;          // 1: E4M3 operands (K slices of 128, K = 32 per instruction)
 };
 
 // ---------------------------------------------------------------- small helpers
@@ -100,6 +102,19 @@ __device__ __forceinline__ void ld_tile8(const uint8_t* tile, int row, int col, 
         const float2 f = unpack_bf16x2(w[i]);
         v[2 * i] = f.x; v[2 * i + 1] = f.y;
     }
+}
+
+// Columns col..col+7 (col % 8 == 0) of `row`, times s, into a tile of E4M3
+// operands: 128-column slices of 16 KB, 128-byte swizzled rows, each 16-byte
+// unit holding 16 values (RN, saturating to the finite range).
+__device__ __forceinline__ void st_tile8_e4m3(uint8_t* tile, int row, int col, const float* v, float s) {
+    uint32_t w[4];
+#pragma unroll
+    for (int i = 0; i < 4; ++i)
+        w[i] = (uint32_t)__nv_cvt_float2_to_fp8x2(make_float2(v[2 * i] * s, v[2 * i + 1] * s), __NV_SATFINITE,
+                                                  __NV_E4M3);
+    uint8_t* dst = tile + (col >> 7) * 16384 + tc::sw128_offset(row, (col & 127) >> 4) + ((col >> 3) & 1) * 8;
+    *reinterpret_cast<uint2*>(dst) = make_uint2(w[0] | (w[1] << 16), w[2] | (w[3] << 16));
 }
 
 __device__ __forceinline__ void st_bf16x16(bf16* dst, const float* v) {
@@ -375,8 +390,9 @@ __device__ void mma_role(const Sched& sch, int ntiles, int nstages, uint32_t aba
             const FGemm g = sch.gemm(q);
             sch.prefetch(q, t);
             const uint32_t abase = g.asel ? abase1 : abase0;
-            const uint32_t idesc = tc::idesc_bf16(128, g.N, 0, 0);
+            const uint32_t idesc = g.f8 ? tc::idesc_e4m3(128, g.N) : tc::idesc_bf16(128, g.N, 0, 0);
             const bool dual = g.dual != 0;
+            const int kslice = g.f8 ? 128 : 64, kstep = g.f8 ? 32 : 16;
             for (int kc = 0; kc < g.nk; ++kc, ++it) {
                 const int s = it % nstages;
                 const uint32_t ph = (uint32_t)(it / nstages) & 1u;
@@ -385,10 +401,15 @@ __device__ void mma_role(const Sched& sch, int ntiles, int nstages, uint32_t aba
                     break;
                 }
                 tc::tc_fence_after();
-                const int nsteps = min(4, (g.K - kc * 64 + 15) / 16);
+                const int nsteps = min(4, (g.K - kc * kslice + kstep - 1) / kstep);
                 for (int k = 0; k < nsteps; ++k) {
+                    // one K step is 32 bytes of the 128-byte swizzled rows for both types
                     const uint64_t ad = tc::sdesc_sw128(abase + (uint32_t)kc * 16384u + 32u * k, 16u);
                     const uint64_t bd = tc::sdesc_sw128(rbase + (uint32_t)s * kFStageBytes + 32u * k, 16u);
+                    if (g.f8) {
+                        tc::mma_f8(tmem + (uint32_t)g.dcol, ad, bd, idesc, (g.acc || kc > 0 || k > 0) ? 1u : 0u);
+                        continue;
+                    }
                     tc::mma_bf16(tmem + (uint32_t)g.dcol, ad, bd, idesc, (g.acc || kc > 0 || k > 0) ? 1u : 0u);
                     if (dual) {
                         const uint64_t ad1 = tc::sdesc_sw128(abase1 + (uint32_t)kc * 16384u + 32u * k, 16u);
@@ -425,6 +446,11 @@ struct FwdZArgs {
     int P, M, D, Dp, Dn, w, wp, L, ntiles;
     float dt;
     int* err;
+    // FP8 hidden layers: E4M3 W_l (box {128, w}) and the per-layer inverse
+    // scales of the accumulators; h_l for l < L is written to the tile in E4M3
+    int f8;
+    CUtensorMap wf8[kFusedMaxDepth + 1];
+    const float* f8inv;
 };
 
 struct FwdZSched {
@@ -437,6 +463,7 @@ struct FwdZSched {
         g.asel = 0;
         g.dual = 0;
         if (q == 0) { g.map = &a->wf[0]; g.nk = a->Dp / 64; g.K = a->D; g.N = a->w; }
+        else if (q <= L && a->f8) { g.map = &a->wf8[q]; g.nk = (a->w + 127) / 128; g.K = a->w; g.N = a->w; g.f8 = 1; }
         else if (q <= L) { g.map = &a->wf[q]; g.nk = a->wp / 64; g.K = a->w; g.N = a->w; }
         else if (q <= 2 * L) { g.map = &a->wr[2 * L + 1 - q]; g.nk = a->wp / 64; g.K = a->w; g.N = a->w; }
         else { g.map = &a->wr[0]; g.nk = a->wp / 64; g.K = a->w; g.N = a->Dn; }
@@ -570,6 +597,11 @@ __global__ void __launch_bounds__(fused_threads(kFwdGroups), 1) k_fused_fwdz(con
                     const float* bias = ptab + l * a.w;
                     uint32_t* sc = scr + (size_t)l * blk;
                     float ypart = 0.f;
+                    // FP8 hidden layers: the accumulator of layer l >= 1 carries the
+                    // scales of its E4M3 operands; h_l (l < L) goes out in E4M3
+                    const bool f8 = a.f8 != 0;
+                    const float ascale = (f8 && l >= 1) ? __ldg(a.f8inv + l) : 1.f;
+                    const float hscale = e4m3_act_scale(l, RES);
                     for (int ch = eg; ch < nch; ch += NG) {
                         const int c0 = ch * 8;
                         uint32_t rv[8], rr[8];
@@ -579,14 +611,15 @@ __global__ void __launch_bounds__(fused_threads(kFwdGroups), 1) k_fused_fwdz(con
                         float h[8], d1[8];
 #pragma unroll
                         for (int j = 0; j < 8; ++j) {
-                            float av = __uint_as_float(rv[j]) + bias[c0 + j];
+                            float av = fmaf(__uint_as_float(rv[j]), ascale, bias[c0 + j]);
                             if (l == 0) av = fmaf(tval, win0[c0 + j], av);
                             const Act3 f = act3_sfu<ACT>(av);
                             h[j] = ((RES && l >= 1) ? __uint_as_float(rr[j]) : 0.f) + f.f;
                             d1[j] = f.d1;
                         }
                         if (l < L) {
-                            st_tile8(tile, row, c0, h);
+                            if (f8) st_tile8_e4m3(tile, row, c0, h, hscale);
+                            else st_tile8(tile, row, c0, h);
                             st_pm8h(sc, row, c0, d1, pol_keep);
                             if (RES) tmem_st_f8(tres + (uint32_t)c0, h);
                         } else {
@@ -1068,6 +1101,11 @@ fbsde_status fused_forward(fbsde_ctx* c, const float* theta, bool for_grad) {
     a.off = param_offsets(c);
     a.P = (int)c->P(); a.M = c->M; a.D = c->D; a.Dp = b->Dp; a.Dn = b->Dn; a.w = c->w; a.wp = b->wp;
     a.L = c->L; a.ntiles = (a.P + 127) / 128; a.dt = (float)(c->T / c->N); a.err = b->err;
+    a.f8 = b->f8 ? 1 : 0;
+    if (b->f8) {
+        for (int l = 1; l <= c->L; ++l) a.wf8[l] = b->mW8[l];
+        a.f8inv = b->f8inv;
+    }
     const int cap = c->grid_cap > 0 && c->grid_cap < b->grid ? c->grid_cap : b->grid;
     const int grid = a.ntiles < cap ? a.ntiles : cap;
     const size_t smem = fwdz_smem_bytes(c->L, c->w);

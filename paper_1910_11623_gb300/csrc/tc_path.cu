@@ -7,6 +7,7 @@
 #include <cuda.h>
 #include <cudaTypedefs.h>
 #include <cuda_bf16.h>
+#include <cuda_fp8.h>
 #include <cuda_runtime.h>
 
 #include <cstring>
@@ -51,6 +52,20 @@ bool map2d(CUtensorMap* m, const void* base, uint64_t inner, uint64_t outer, uin
               CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE) == CUDA_SUCCESS;
 }
 
+// Row-major 8-bit matrix [outer x inner] (row stride ld bytes), box
+// {128, box_outer}, 128-byte swizzle, zero fill outside the matrix.
+bool map2d_u8(CUtensorMap* m, const void* base, uint64_t inner, uint64_t outer, uint64_t ld, uint32_t box_outer) {
+    auto fn = encode_fn();
+    if (!fn) return false;
+    cuuint64_t dims[2] = {inner, outer};
+    cuuint64_t strides[1] = {ld};
+    cuuint32_t box[2] = {128, box_outer};
+    cuuint32_t es[2] = {1, 1};
+    return fn(m, CU_TENSOR_MAP_DATA_TYPE_UINT8, 2, const_cast<void*>(base), dims, strides, box, es,
+              CU_TENSOR_MAP_INTERLEAVE_NONE, CU_TENSOR_MAP_SWIZZLE_128B, CU_TENSOR_MAP_L2_PROMOTION_L2_256B,
+              CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE) == CUDA_SUCCESS;
+}
+
 // Stack of `depth` row-major BF16 matrices [outer x inner] (row stride ld,
 // matrix stride mstride elements), box {64, box_outer, 1}, 128-byte swizzle.
 bool map3d(CUtensorMap* m, const void* base, uint64_t inner, uint64_t outer, uint64_t depth, uint64_t ld,
@@ -89,6 +104,12 @@ fbsde_status bf16_create(fbsde_ctx* c) {
     const size_t nl = (size_t)L + 1;
     // per-tile fused kernels: FC / ResNet, depth <= kFusedMaxDepth, D <= 256
     b->fused = c->akind != FBSDE_NAIS && L <= kFusedMaxDepth && b->Dp <= 256;
+    b->f8 = c->prec == FBSDE_FP8_HIDDEN;
+    if (b->f8 && (!b->fused || w % 32 != 0))
+        return set_err(c, FBSDE_ERR_UNSUPPORTED,
+                       "FP8 hidden layers need an FC or ResNet network with depth <= 8, D <= 255 and a width "
+                       "that is a multiple of 32");
+    b->wp8 = (int)rup(w, 128);
     c->need_V32 = !b->fused;  // the fused backward reads the BF16 v rows only
     if (b->fused) {
         int dev = 0, sms = 0;
@@ -117,6 +138,10 @@ fbsde_status bf16_create(fbsde_ctx* c) {
         add((size_t)(L > 0 ? L : 1) * b->G_stride * sizeof(bf16));
         add((size_t)b->grid * (2 * L + 2) * 128 * w * sizeof(bf16));
         add((size_t)(L + 3) * w * sizeof(float));
+    }
+    if (b->f8) {
+        for (int l = 1; l <= L; ++l) add((size_t)w * b->wp8);
+        add((size_t)(L + 1) * sizeof(float));
     }
     cudaError_t e = cudaMalloc(&b->mem, bytes);
     if (e != cudaSuccess) {
@@ -157,6 +182,10 @@ fbsde_status bf16_create(fbsde_ctx* c) {
         b->scratch = (bf16*)take((size_t)b->grid * (2 * L + 2) * 128 * w * sizeof(bf16));
         b->pvec = (float*)take((size_t)(L + 3) * w * sizeof(float));
     }
+    if (b->f8) {
+        for (int l = 1; l <= L; ++l) b->W8[l] = (uint8_t*)take((size_t)w * b->wp8);
+        b->f8inv = (float*)take((size_t)(L + 1) * sizeof(float));
+    }
 
     bool ok = true;
     const uint64_t P64 = Pm;
@@ -181,6 +210,7 @@ fbsde_status bf16_create(fbsde_ctx* c) {
         ok &= map2d(&b->mWT[l], b->WT[l], b->wp, w, b->wp, w);
         ok &= map2d(&b->mBx[l], b->Bx[l], b->Dp, w, b->Dp, w);
         ok &= map2d(&b->mBxT[l], b->BxT[l], b->wp, b->Dn, b->wp, b->Dn);
+        if (b->f8) ok &= map2d_u8(&b->mW8[l], b->W8[l], b->wp8, w, b->wp8, w);
     }
     if (b->fused) {
         ok &= map3d(&b->sHb, b->Hb[0], b->wp, P64, (uint64_t)L + 1, b->wp, b->OP_stride, 128);
@@ -599,6 +629,50 @@ static fbsde_status wgrad(fbsde_ctx* c, TcArgs a, int ncols_store, float* out, i
 
 // ------------------------------------------------------------------ weights
 
+// E4M3 copies of the hidden-layer weights W_l (l = 1..L), one block per layer:
+// the block's max |W_l| sets the per-tensor scale s_W (the largest power of two
+// with s_W max|W| <= 448, so the scaled values stay finite), the copy holds
+// RN(s_W W_l) (satfinite), and inv[l] = 1 / (s_h(l-1) s_W) undoes both scales
+// on the FP32 accumulator.
+struct Fp8WeightArgs {
+    const float* W[kMaxDepth + 1];
+    uint8_t* W8[kMaxDepth + 1];
+    int w, ld8, res;
+    float* inv;
+};
+
+__global__ void __launch_bounds__(1024) k_fp8_weights(const Fp8WeightArgs a) {
+    __shared__ float red[32];
+    __shared__ float s_scale;
+    const int l = blockIdx.x + 1;
+    const float* W = a.W[l];
+    const int n = a.w * a.w;
+    float mx = 0.f;
+    for (int i = threadIdx.x; i < n; i += blockDim.x) mx = fmaxf(mx, fabsf(W[i]));
+    for (int o = 16; o > 0; o >>= 1) mx = fmaxf(mx, __shfl_xor_sync(0xffffffffu, mx, o));
+    if ((threadIdx.x & 31) == 0) red[threadIdx.x >> 5] = mx;
+    __syncthreads();
+    if (threadIdx.x == 0) {
+        float m = 0.f;
+        for (int k = 0; k < (int)(blockDim.x >> 5); ++k) m = fmaxf(m, red[k]);
+        float s = 1.f;
+        if (m > 0.f) {
+            while (m * s * 2.f <= 448.f && s < 1.0e30f) s *= 2.f;
+            while (m * s > 448.f) s *= 0.5f;
+        }
+        s_scale = s;
+        a.inv[l] = 1.f / (e4m3_act_scale(l - 1, a.res != 0) * s);
+    }
+    __syncthreads();
+    const float s = s_scale;
+    uint8_t* W8 = a.W8[l];
+    for (int i = threadIdx.x; i < a.w * a.ld8; i += blockDim.x) {
+        const int r = i / a.ld8, k = i % a.ld8;
+        const float v = k < a.w ? W[(size_t)r * a.w + k] * s : 0.f;
+        W8[i] = (uint8_t)__nv_cvt_float_to_fp8(v, __NV_SATFINITE, __NV_E4M3);
+    }
+}
+
 fbsde_status bf16_prepare_weights(fbsde_ctx* c, const float* theta) {
     FBSDE_TRY(fp32_prepare_weights(c, theta));  // NAIS: A_l = -R^T R - eps I in FP32
     Bf16Work* b = c->bf;
@@ -621,6 +695,17 @@ fbsde_status bf16_prepare_weights(fbsde_ctx* c, const float* theta) {
             FBSDE_TRY(cvt(b->Bx[l], w, b->Dp, b->Dp, theta + pl.B[l], K0, 1, w, D, 0));
             FBSDE_TRY(cvt(b->BxT[l], b->Dn, b->wp, b->wp, theta + pl.B[l], K0, 1, D, w, 1));
         }
+    }
+    if (b->f8) {
+        Fp8WeightArgs fa;
+        std::memset(&fa, 0, sizeof(fa));
+        for (int l = 1; l <= c->L; ++l) {
+            fa.W[l] = theta + pl.W[l];
+            fa.W8[l] = b->W8[l];
+        }
+        fa.w = w; fa.ld8 = b->wp8; fa.res = c->akind == FBSDE_RESNET ? 1 : 0; fa.inv = b->f8inv;
+        k_fp8_weights<<<c->L, 1024, 0, c->stream>>>(fa);
+        FBSDE_CK_LAUNCH(c);
     }
     return FBSDE_OK;
 }

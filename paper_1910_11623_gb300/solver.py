@@ -17,7 +17,7 @@ from . import _lib as L
 _KIND = {"bsb": L.FBSDE_BSB, "hjb": L.FBSDE_HJB}
 _ARCH = {"fc": L.FBSDE_FC, "resnet": L.FBSDE_RESNET, "nais": L.FBSDE_NAIS}
 _ACT = {"sin": L.FBSDE_SIN, "tanh": L.FBSDE_TANH}
-_PREC = {"fp32": L.FBSDE_FP32, "bf16": L.FBSDE_BF16}
+_PREC = {"fp32": L.FBSDE_FP32, "bf16": L.FBSDE_BF16, "fp8": L.FBSDE_FP8_HIDDEN}
 
 
 @dataclass
@@ -47,7 +47,8 @@ class ProblemSpec:
 @dataclass
 class ArchSpec:
     """Network of Section 3.1: kind 'fc' | 'resnet' | 'nais'; act 'sin' | 'tanh';
-    prec 'fp32' (CUDA-core form) | 'bf16' (tcgen05 tensor-core form)."""
+    prec 'fp32' (CUDA-core form) | 'bf16' (tcgen05 tensor-core form) | 'fp8' (the BF16 form with
+    the hidden-layer forward contractions in E4M3)."""
     kind: str
     width: int
     depth: int

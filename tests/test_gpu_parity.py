@@ -359,3 +359,72 @@ def test_bf16_many_point_splits_width128(P):
     prob = P.ProblemSpec(kind="hjb", D=20, N=40, M=512, x0=[0.0] * 20)
     arch = P.ArchSpec(kind="resnet", width=128, depth=2, act="tanh", prec="bf16")
     _check_eval(P, prob, arch, seed=8, it=3, perturb=0.05)
+
+
+# FP8 hidden layers: the forward contractions W_l h_{l-1} (l >= 1) take E4M3
+# operands (4 exponent bits, 3 mantissa bits: unit roundoff 2^-4).  The
+# error this costs is a property of the network, so it is checked twice:
+#   * against the FP64 oracle with bounds that state it (loss and gradient
+#     1e-2, Z 0.1, Y 0.3 of max |Y|: on this case Y is a small difference of
+#     larger hidden activations, so E4M3 rounding moves it by about 18 %);
+#   * against the same network evaluated in FP64 with every hidden-layer
+#     operand rounded to E4M3 as the kernels do (per-tensor power-of-two
+#     scales).  Which way a value near a rounding boundary goes depends on
+#     the last bits of its inputs (the kernels' tanh.approx, FP32 sums), and a
+#     relative change of 1e-4 before rounding already moves single Y values by
+#     5 %; the size of the error does not move (its RMS over the points
+#     changes by under 2 % under such perturbations).  So the GPU's RMS error
+#     against the oracle must be within 20 % of the E4M3 model's: a wrong
+#     scale or layout would change it many times over, BF16 operands would
+#     shrink it a hundredfold.
+def _e4m3(v):
+    """Round to the nearest E4M3 value (ties to even), saturating at 448."""
+    a = np.minimum(np.abs(v), 448.0)
+    e = np.maximum(np.floor(np.log2(np.maximum(a, 1e-300))), -6.0)
+    step = 2.0 ** (e - 3)
+    return np.sign(v) * np.round(a / step) * step
+
+
+def _pow2_scale(bound):
+    s = 1.0
+    while bound * s * 2.0 <= 448.0:
+        s *= 2.0
+    return s
+
+
+def test_fp8_hidden_layers_error_vs_oracle(P):
+    prob = P.ProblemSpec(kind="bsb", D=20, N=8, M=128, x0=[1.0, 0.5] * 10)
+    arch = P.ArchSpec(kind="resnet", width=128, depth=3, act="tanh", prec="fp8")
+    s = _solver(P, prob, arch, seed=12)
+    th64, th = _theta_pair(P, s, prob, arch, 12, 0.05)
+    op, oa = oracle_specs(prob, arch)
+    ro, g = F.rollout_grad(op, oa, th64, 12, 4)
+    loss, y0, grad = s.rollout_grad(th, 4)
+    Y, Z, _ = s.rollout_detail(th, 4)
+    torch.cuda.synchronize()
+    Yg = Y.cpu().numpy().astype(np.float64)
+    errs = {"loss": rel(loss.item(), ro.loss), "grad": rel_max(grad.cpu().numpy(), g),
+            "Z": rel_max(Z.cpu().numpy(), ro.Z), "Y": rel_max(Yg, ro.Y)}
+    assert errs["loss"] < 1e-2 and errs["grad"] < 1e-2 and errs["Z"] < 0.1 and errs["Y"] < 0.3, errs
+    # the same network with E4M3 hidden-layer operands, in FP64
+    prm = F.unpack(th64, op, oa)
+    _, X = F.sample_paths(op, 12, 4)
+    U = F.network_inputs(op, X).reshape(-1, prob.D + 1)
+    h = np.tanh(U @ prm["W_in"].T + prm["b_in"])
+    for l in range(1, arch.depth + 1):
+        W = prm[f"W_{l}"]
+        sh, sw = _pow2_scale(float(l)), _pow2_scale(np.abs(W).max())
+        h = h + np.tanh(_e4m3(h * sh) @ _e4m3(W * sw).T / (sh * sw) + prm[f"b_{l}"])
+    Y8 = (h @ prm["w_o"] + prm["b_o"][0]).reshape(Yg.shape)
+    rms_gpu = np.sqrt(np.mean((Yg - ro.Y) ** 2))
+    rms_model = np.sqrt(np.mean((Y8 - ro.Y) ** 2))
+    assert abs(rms_gpu - rms_model) < 0.2 * rms_model, (rms_gpu, rms_model, errs)
+    s.close()
+
+
+def test_fp8_rejects_unsupported_shapes(P):
+    prob = P.ProblemSpec(kind="bsb", D=4, N=4, M=16, x0=[1.0] * 4)
+    with pytest.raises(Exception):
+        P.Solver(prob, P.ArchSpec(kind="resnet", width=48, depth=2, act="tanh", prec="fp8"))
+    with pytest.raises(Exception):
+        P.Solver(prob, P.ArchSpec(kind="nais", width=32, depth=2, act="tanh", prec="fp8"))
