@@ -374,7 +374,9 @@ __device__ void producer_role(const Sched& sch, int ntiles, int nstages, uint8_t
 // Warp 1, one lane: per contraction wait for the operand tile, then issue
 // K = 16 MMAs slice by slice, releasing each ring stage and finally
 // signalling the accumulator.
-template <class Sched>
+// F8: the schedule may contain E4M3 contractions (FGemm::f8); without it
+// the loop is the BF16 one only.
+template <bool F8, class Sched>
 __device__ void mma_role(const Sched& sch, int ntiles, int nstages, uint32_t abase0, uint32_t abase1,
                          uint32_t rbase, uint32_t tmem, uint64_t* bfull, uint64_t* bempty, uint64_t* accf,
                          uint64_t* aready, volatile int* abort_flag, int* err) {
@@ -390,9 +392,9 @@ __device__ void mma_role(const Sched& sch, int ntiles, int nstages, uint32_t aba
             const FGemm g = sch.gemm(q);
             sch.prefetch(q, t);
             const uint32_t abase = g.asel ? abase1 : abase0;
-            const uint32_t idesc = g.f8 ? tc::idesc_e4m3(128, g.N) : tc::idesc_bf16(128, g.N, 0, 0);
+            const bool f8 = F8 && g.f8 != 0;
+            const uint32_t idesc = f8 ? tc::idesc_e4m3(128, g.N) : tc::idesc_bf16(128, g.N, 0, 0);
             const bool dual = g.dual != 0;
-            const int kslice = g.f8 ? 128 : 64, kstep = g.f8 ? 32 : 16;
             for (int kc = 0; kc < g.nk; ++kc, ++it) {
                 const int s = it % nstages;
                 const uint32_t ph = (uint32_t)(it / nstages) & 1u;
@@ -401,12 +403,13 @@ __device__ void mma_role(const Sched& sch, int ntiles, int nstages, uint32_t aba
                     break;
                 }
                 tc::tc_fence_after();
-                const int nsteps = min(4, (g.K - kc * kslice + kstep - 1) / kstep);
+                // K per slice 64 (BF16) or 128 (E4M3); one K step is 32 bytes of
+                // the 128-byte swizzled rows for both types
+                const int nsteps = f8 ? min(4, (g.K - kc * 128 + 31) / 32) : min(4, (g.K - kc * 64 + 15) / 16);
                 for (int k = 0; k < nsteps; ++k) {
-                    // one K step is 32 bytes of the 128-byte swizzled rows for both types
                     const uint64_t ad = tc::sdesc_sw128(abase + (uint32_t)kc * 16384u + 32u * k, 16u);
                     const uint64_t bd = tc::sdesc_sw128(rbase + (uint32_t)s * kFStageBytes + 32u * k, 16u);
-                    if (g.f8) {
+                    if (F8 && f8) {
                         tc::mma_f8(tmem + (uint32_t)g.dcol, ad, bd, idesc, (g.acc || kc > 0 || k > 0) ? 1u : 0u);
                         continue;
                     }
@@ -480,7 +483,7 @@ struct FwdZSched {
     }
 };
 
-template <int ACT, bool RES>
+template <int ACT, bool RES, bool F8>
 __global__ void __launch_bounds__(fused_threads(kFwdGroups), 1) k_fused_fwdz(const __grid_constant__ FwdZArgs a) {
     constexpr int NG = kFwdGroups, NE = 128 * NG;
     extern __shared__ uint8_t smem_raw[];
@@ -532,7 +535,7 @@ __global__ void __launch_bounds__(fused_threads(kFwdGroups), 1) k_fused_fwdz(con
         if (lane == 0) producer_role(sch, a.ntiles, kFwdStages, ring, bfull, bempty, abort_flag, a.err);
     } else if (warp == 1) {
         if (lane == 0)
-            mma_role(sch, a.ntiles, kFwdStages, tc::smem_u32(tile), tc::smem_u32(tile), tc::smem_u32(ring), tmem,
+            mma_role<F8>(sch, a.ntiles, kFwdStages, tc::smem_u32(tile), tc::smem_u32(tile), tc::smem_u32(ring), tmem,
                      bfull, bempty, accf, aready, abort_flag, a.err);
     } else {
         const int eg = (warp - 2) >> 2;  // epilogue group: chunks eg, eg + NG, ...
@@ -599,9 +602,9 @@ __global__ void __launch_bounds__(fused_threads(kFwdGroups), 1) k_fused_fwdz(con
                     float ypart = 0.f;
                     // FP8 hidden layers: the accumulator of layer l >= 1 carries the
                     // scales of its E4M3 operands; h_l (l < L) goes out in E4M3
-                    const bool f8 = a.f8 != 0;
-                    const float ascale = (f8 && l >= 1) ? __ldg(a.f8inv + l) : 1.f;
-                    const float hscale = e4m3_act_scale(l, RES);
+                    const bool f8 = F8 && a.f8 != 0;
+                    const float ascale = (F8 && f8 && l >= 1) ? __ldg(a.f8inv + l) : 1.f;
+                    const float hscale = F8 ? e4m3_act_scale(l, RES) : 1.f;
                     for (int ch = eg; ch < nch; ch += NG) {
                         const int c0 = ch * 8;
                         uint32_t rv[8], rr[8];
@@ -611,14 +614,15 @@ __global__ void __launch_bounds__(fused_threads(kFwdGroups), 1) k_fused_fwdz(con
                         float h[8], d1[8];
 #pragma unroll
                         for (int j = 0; j < 8; ++j) {
-                            float av = fmaf(__uint_as_float(rv[j]), ascale, bias[c0 + j]);
+                            float av = F8 ? fmaf(__uint_as_float(rv[j]), ascale, bias[c0 + j])
+                                          : __uint_as_float(rv[j]) + bias[c0 + j];
                             if (l == 0) av = fmaf(tval, win0[c0 + j], av);
                             const Act3 f = act3_sfu<ACT>(av);
                             h[j] = ((RES && l >= 1) ? __uint_as_float(rr[j]) : 0.f) + f.f;
                             d1[j] = f.d1;
                         }
                         if (l < L) {
-                            if (f8) st_tile8_e4m3(tile, row, c0, h, hscale);
+                            if (F8 && f8) st_tile8_e4m3(tile, row, c0, h, hscale);
                             else st_tile8(tile, row, c0, h);
                             st_pm8h(sc, row, c0, d1, pol_keep);
                             if (RES) tmem_st_f8(tres + (uint32_t)c0, h);
@@ -847,7 +851,7 @@ __global__ void __launch_bounds__(bwd_threads(), 1) k_fused_bwd(const __grid_con
             if (lane == 0) producer_role(sch, a.ntiles, kBwdStages, ring, bfull, bempty, abort_flag, a.err);
         } else if (warp == 1) {
             if (lane == 0)
-                mma_role(sch, a.ntiles, kBwdStages, tc::smem_u32(tile_h), tc::smem_u32(tile_d), tc::smem_u32(ring),
+                mma_role<false>(sch, a.ntiles, kBwdStages, tc::smem_u32(tile_h), tc::smem_u32(tile_d), tc::smem_u32(ring),
                          tmem, bfull, bempty, accf, aready, abort_flag, a.err);
         }
     } else {
@@ -1113,12 +1117,20 @@ fbsde_status fused_forward(fbsde_ctx* c, const float* theta, bool for_grad) {
     const bool res = c->akind == FBSDE_RESNET;
     const int tok = prof_begin(c, PROF_POINTS);
     cudaError_t e;
-    if (c->act == FBSDE_TANH)
-        e = res ? launch_fused(k_fused_fwdz<FBSDE_TANH, true>, a, grid, FT, smem, c->stream)
-                : launch_fused(k_fused_fwdz<FBSDE_TANH, false>, a, grid, FT, smem, c->stream);
-    else
-        e = res ? launch_fused(k_fused_fwdz<FBSDE_SIN, true>, a, grid, FT, smem, c->stream)
-                : launch_fused(k_fused_fwdz<FBSDE_SIN, false>, a, grid, FT, smem, c->stream);
+    if (b->f8) {
+        if (c->act == FBSDE_TANH)
+            e = res ? launch_fused(k_fused_fwdz<FBSDE_TANH, true, true>, a, grid, FT, smem, c->stream)
+                    : launch_fused(k_fused_fwdz<FBSDE_TANH, false, true>, a, grid, FT, smem, c->stream);
+        else
+            e = res ? launch_fused(k_fused_fwdz<FBSDE_SIN, true, true>, a, grid, FT, smem, c->stream)
+                    : launch_fused(k_fused_fwdz<FBSDE_SIN, false, true>, a, grid, FT, smem, c->stream);
+    } else if (c->act == FBSDE_TANH) {
+        e = res ? launch_fused(k_fused_fwdz<FBSDE_TANH, true, false>, a, grid, FT, smem, c->stream)
+                : launch_fused(k_fused_fwdz<FBSDE_TANH, false, false>, a, grid, FT, smem, c->stream);
+    } else {
+        e = res ? launch_fused(k_fused_fwdz<FBSDE_SIN, true, false>, a, grid, FT, smem, c->stream)
+                : launch_fused(k_fused_fwdz<FBSDE_SIN, false, false>, a, grid, FT, smem, c->stream);
+    }
     // algorithmic flops: lift + L layers forward, L reverse layers and the Z contraction
     const double P = a.P, w = a.w, D = a.D;
     prof_end(c, PROF_POINTS, tok, 2.0 * P * w * (2.0 * D + 2.0 * c->L * w));
