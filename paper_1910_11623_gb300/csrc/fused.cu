@@ -5,28 +5,32 @@
 //   * activation tiles (BF16, 128 rows x up to 256 columns) live in shared
 //     memory in the 128-byte-swizzled K-major layout the tensor cores read,
 //     and each layer's epilogue rewrites them in place;
-//   * the ResNet residual stream (FP32) lives in TMEM columns 256..511 next
-//     to the accumulator (columns 0..255);
+//   * the forward kernel keeps the ResNet residual stream (FP32) in TMEM
+//     columns 256..511 next to the accumulator (columns 0..255); the
+//     backward kernel holds two accumulators there (forward recomputation
+//     and tangent) and accumulates the adjoint h-bar in place;
 //   * the weights stream from L2 through a TMA ring, one 64-wide K slice per
 //     stage, in the order the layers consume them, so the next layer's
 //     weights arrive while the current epilogue runs;
 //   * per-layer derivatives needed later in the tile go to a per-CTA scratch
 //     region that the same CTA reads back within microseconds.
-// Warp 0 issues the weight TMA loads, warp 1 allocates TMEM and issues
-// tcgen05.mma, warps 2-9 (two groups of four, each group covering the 128
-// TMEM lanes) run the epilogues on alternating 16-column chunks.  The MMA of
-// contraction q+1 starts when all 256 epilogue threads have finished
-// contraction q (mbarrier `aready`): they have read its accumulator and
-// written the operand the next contraction reads.  Every wait is bounded.
+// Warp 0 issues the weight TMA loads and warp 1 allocates TMEM and issues
+// tcgen05.mma from one thread; the epilogue warpgroups (three in the forward
+// kernel from warp 2, two in the backward kernel from warp 4, each covering
+// the 128 TMEM lanes) take alternating 8-column chunks.  The MMA of
+// contraction q+1 starts when every epilogue thread has finished contraction
+// q (mbarrier `aready`): they have read its accumulator and written the
+// operand the next contraction reads.  Every wait is bounded.
 //
 // k_fused_fwdz (Section 2.2: Y = u(t, X) and Z = grad_x u by the reverse
 // pass): lift, L layers, the reverse sweep through the L layers and the Z
-// contraction; outputs Y, Z and g_l (BF16, l < L) for the gradient.
+// contraction; outputs Y, Z and g_l (BF16, l < L) for the gradient.  Its F8
+// variant runs the hidden-layer forward contractions on E4M3 operands.
 //
 // k_fused_bwd (the derivative of the loss of Eq. "loss" through Y_n and Z_n):
 // per layer the forward contraction (recomputed) and the tangent contraction
 // along (0, v), then the adjoint sweep down the layers; outputs the operands
-// of the weight-gradient contractions: h_l, h'_l, e_l, abar_l (BF16).
+// of the weight-gradient contractions: h_l, h'_l, abar_l (BF16).
 #include <cuda.h>
 #include <cuda_bf16.h>
 #include <cuda_fp8.h>
