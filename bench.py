@@ -314,6 +314,18 @@ def multilevel_run(P, w, target, max_steps):
     return res
 
 
+# ----------------------------------------------------------------- replicas
+
+def replica_seed(base_seed: int, rank: int) -> int:
+    """Each rank trains an independent replica: its own noise and Theta_0."""
+    return base_seed + rank
+
+
+def job_throughput(world: int, steps_per_rank: int, ms_max: float) -> float:
+    """Whole-job iterations/s: all ranks' steps over the slowest rank's time."""
+    return world * steps_per_rank / (ms_max / 1000.0)
+
+
 def main():
     args = parse_args()
     world = int(os.environ.get("WORLD_SIZE", "1"))
@@ -344,7 +356,7 @@ def main():
         from dataclasses import replace as _replace
         w = _replace(w, problem=_replace(w.problem, M=args.M))
     stream = torch.cuda.Stream()
-    solver = P.Solver(w.problem, w.arch, seed=w.seed + rank, stream=stream)
+    solver = P.Solver(w.problem, w.arch, seed=replica_seed(w.seed, rank), stream=stream)
     theta = solver.init_params()
     m, v = torch.zeros_like(theta), torch.zeros_like(theta)
     with torch.cuda.stream(stream):
@@ -391,7 +403,7 @@ def main():
     if world > 1:
         dist.all_reduce(t, op=dist.ReduceOp.MAX)
     ms_max = float(t.item())
-    value = world * timed_steps / (ms_max / 1000.0)
+    value = job_throughput(world, timed_steps, ms_max)
 
     # end to end through the public API: per step, x0 from pinned host memory
     # to the device, the training step, and the loss / Y0 back to the host.
@@ -423,7 +435,7 @@ def main():
     te = torch.tensor([e2e_s], device="cuda")
     if world > 1:
         dist.all_reduce(te, op=dist.ReduceOp.MAX)
-    e2e = {"value": world * e2e_steps / float(te.item()), "unit": "it/s",
+    e2e = {"value": job_throughput(world, e2e_steps, 1000.0 * float(te.item())), "unit": "it/s",
            "h2d_bytes_per_step": D * 4, "d2h_bytes_per_step": 8}
 
     out = None
@@ -492,7 +504,7 @@ def main():
         del solver
         torch.cuda.empty_cache()
         w32 = w.with_prec("fp32")
-        s32 = P.Solver(w32.problem, w32.arch, seed=w.seed + rank)
+        s32 = P.Solver(w32.problem, w32.arch, seed=replica_seed(w.seed, rank))
         th32 = s32.init_params()
         m32, v32 = torch.zeros_like(th32), torch.zeros_like(th32)
         for s in range(1, 3):
@@ -503,7 +515,7 @@ def main():
         if world > 1:
             dist.all_reduce(t, op=dist.ReduceOp.MAX)
         if out is not None:
-            v32rate = world * args.fp32_steps / (float(t.item()) / 1000.0)
+            v32rate = job_throughput(world, args.fp32_steps, float(t.item()))
             out["fp32_form"] = {"value": v32rate, "unit": "it/s", "steps": args.fp32_steps}
             out["speedup_vs_fp32_form"] = value / v32rate
         del s32
@@ -514,7 +526,7 @@ def main():
     if args.form == "bf16" and args.fp8_steps > 0:
         try:
             w8 = w.with_prec("fp8")
-            s8 = P.Solver(w8.problem, w8.arch, seed=w.seed + rank, stream=torch.cuda.Stream())
+            s8 = P.Solver(w8.problem, w8.arch, seed=replica_seed(w.seed, rank), stream=torch.cuda.Stream())
             th8 = s8.init_params()
             m8, v8 = torch.zeros_like(th8), torch.zeros_like(th8)
             with torch.cuda.stream(s8.stream):
