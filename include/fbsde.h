@@ -86,7 +86,7 @@ typedef enum { FBSDE_SIN = 0, FBSDE_TANH = 1 } fbsde_act;
  * that gives Y, Z and the loss) in FP8 E4M3 with per-tensor scales and FP32
  * accumulation; the lift, the Z pass, the gradient sweeps and the weight
  * gradients stay BF16.  Needs an FC or ResNet network served by the fused
- * kernels (depth <= 8, width <= 256 and a multiple of 32, D <= 255), else
+ * kernels (depth <= 8, width <= 256 and a multiple of 32, D <= 256), else
  * FBSDE_ERR_UNSUPPORTED at create. */
 typedef enum { FBSDE_FP32 = 0, FBSDE_BF16 = 1, FBSDE_FP8_HIDDEN = 2 } fbsde_prec;
 

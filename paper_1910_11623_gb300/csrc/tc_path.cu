@@ -103,11 +103,14 @@ fbsde_status bf16_create(fbsde_ctx* c) {
     b->OP_stride = rup(Pm * b->wp, 128);
     const size_t nl = (size_t)L + 1;
     // per-tile fused kernels: FC / ResNet, depth <= kFusedMaxDepth, D <= 256
+    if (b->Dn > 256)
+        return set_err(c, FBSDE_ERR_UNSUPPORTED,
+                       "the BF16 forms need D <= 256 (the Z contraction's output width); use the FP32 form");
     b->fused = c->akind != FBSDE_NAIS && L <= kFusedMaxDepth && b->Dp <= 256;
     b->f8 = c->prec == FBSDE_FP8_HIDDEN;
     if (b->f8 && (!b->fused || w % 32 != 0))
         return set_err(c, FBSDE_ERR_UNSUPPORTED,
-                       "FP8 hidden layers need an FC or ResNet network with depth <= 8, D <= 255 and a width "
+                       "FP8 hidden layers need an FC or ResNet network with depth <= 8, D <= 256 and a width "
                        "that is a multiple of 32");
     b->wp8 = (int)rup(w, 128);
     c->need_V32 = !b->fused;  // the fused backward reads the BF16 v rows only

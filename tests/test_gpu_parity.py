@@ -428,3 +428,58 @@ def test_fp8_rejects_unsupported_shapes(P):
         P.Solver(prob, P.ArchSpec(kind="resnet", width=48, depth=2, act="tanh", prec="fp8"))
     with pytest.raises(Exception):
         P.Solver(prob, P.ArchSpec(kind="nais", width=32, depth=2, act="tanh", prec="fp8"))
+
+
+def test_full_size_workload_sampled_against_the_oracle(P):
+    # the measured workload at full size (M = 4096, N = 64, D = 100, ResNet
+    # 5 x 256 tanh) through the same kernels and launch configuration the
+    # bench times: Y, Z and the per-path loss of 16 sampled paths against the
+    # oracle (a path's values depend on that path alone); the loss and the
+    # gradient (sums over all paths) against the FP32 form at the same size,
+    # itself pinned to the oracle at 1e-5 at small sizes
+    w = P.workloads.WORKLOADS["bsb_d100_n64_m4096_resnet5x256_tanh"]
+    wb, wf = w.with_prec("bf16"), w.with_prec("fp32")
+    sb = _solver(P, wb.problem, wb.arch, seed=w.seed)
+    th64, th = _theta_pair(P, sb, wb.problem, wb.arch, w.seed)
+    it = 9
+    Y, Z, pl = sb.rollout_detail(th, it)
+    lb, _, gb = sb.rollout_grad(th, it)
+    torch.cuda.synchronize()
+    idx = np.sort(np.random.default_rng(3).choice(w.problem.M, 16, replace=False))
+    op, oa = oracle_specs(wb.problem, wb.arch)
+    ro = F.rollout_loss(op, oa, th64, w.seed, it, paths=idx)
+    assert rel_max(Y.cpu().numpy()[:, idx].astype(np.float64), ro.Y) < TOL["bf16"]
+    assert rel_max(Z.cpu().numpy()[:, idx].astype(np.float64), ro.Z) < TOL["bf16"]
+    assert rel_max(pl.cpu().numpy()[idx].astype(np.float64), ro.path_loss) < TOL["bf16"]
+    gb = gb.cpu().numpy().astype(np.float64)
+    sb.close()
+    sf = _solver(P, wf.problem, wf.arch, seed=w.seed)
+    lf, _, gf = sf.rollout_grad(th, it)
+    torch.cuda.synchronize()
+    assert rel(lb.item(), lf.item()) < TOL["bf16"]
+    assert rel_max(gb, gf.cpu().numpy().astype(np.float64)) < TOL["bf16"]
+    sf.close()
+
+
+@pytest.mark.parametrize("case", ["D200", "D256", "depth8", "depth9_layered"])
+def test_fused_limits(P, case):
+    # the fused kernels' limits (D <= 256, depth <= 8) and just past the
+    # depth limit, where the layered tcgen05 path takes over
+    D, L = {"D200": (200, 2), "D256": (256, 1), "depth8": (5, 8), "depth9_layered": (5, 9)}[case]
+    x0 = [1.0 if i % 2 == 0 else 0.5 for i in range(D)]
+    prob = P.ProblemSpec(kind="bsb", D=D, N=3, M=16, x0=x0)
+    arch = P.ArchSpec(kind="resnet", width=32, depth=L, act="tanh", prec="bf16")
+    _check_eval(P, prob, arch, seed=21, it=2, perturb=0.05)
+
+
+def test_bf16_rejects_wide_inputs(P):
+    # D > 256: the Z contraction's output would be wider than one tcgen05 tile;
+    # the BF16 forms refuse it at create, the FP32 form serves it
+    prob = P.ProblemSpec(kind="bsb", D=257, N=2, M=8, x0=[1.0] * 257)
+    with pytest.raises(Exception, match="D <= 256"):
+        P.Solver(prob, P.ArchSpec(kind="resnet", width=32, depth=1, act="tanh", prec="bf16"))
+    s = P.Solver(prob, P.ArchSpec(kind="resnet", width=32, depth=1, act="tanh", prec="fp32"))
+    th = s.init_params()
+    loss, _ = s.rollout_loss(th, 1)
+    assert np.isfinite(loss.item())
+    s.close()
