@@ -53,6 +53,8 @@ def parse_args():
                     help="timed loss-only evaluations (forward sweep + residuals), 0: skip")
     ap.add_argument("--fp8-steps", type=int, default=1000,
                     help="Adam steps of the FP8-hidden-layer form (timed for speed, then trained; 0: skip)")
+    ap.add_argument("--nais-steps", type=int, default=5,
+                    help="timed steps of the HJB NAIS-Net workload in both forms (0: skip)")
     ap.add_argument("--batched-steps", type=int, default=3,
                     help="timed group steps of the 32 uneven instances (0: skip)")
     ap.add_argument("--M", type=int, default=0,
@@ -583,6 +585,29 @@ def main():
             for (name, xc), g in zip(cases.items(), got)}
         del sa
         out["multilevel"] = multilevel_run(P, w, target, args.accuracy_steps)
+
+    # the stable network of the paper (NAIS-Net, HJB, Section 4): BF16 and FP32
+    # forms, through the layered tensor-core path
+    if out is not None and args.nais_steps > 0:
+        try:
+            wn = P.workloads.WORKLOADS["hjb_d100_n64_m8192_nais6x256_tanh"]
+            res_n = {"workload": wn.name}
+            for prec in ("bf16", "fp32"):
+                wp_ = wn.with_prec(prec)
+                sn = P.Solver(wp_.problem, wp_.arch, seed=wn.seed, stream=torch.cuda.Stream())
+                thn = sn.init_params()
+                mn, vn = torch.zeros_like(thn), torch.zeros_like(thn)
+                with torch.cuda.stream(sn.stream):
+                    for s_ in range(1, 3):
+                        sn.train_step(thn, mn, vn, s_, wn.lr)
+                msn = time_steps(sn, thn, mn, vn, 3, args.nais_steps, wn.lr)
+                res_n[prec] = {"value": args.nais_steps / (msn / 1000.0), "unit": "it/s"}
+                sn.close()
+                torch.cuda.empty_cache()
+            res_n["speedup_bf16_vs_fp32"] = res_n["bf16"]["value"] / res_n["fp32"]["value"]
+            out["nais_hjb"] = res_n
+        except Exception as exc:
+            out["nais_hjb"] = {"error": f"{type(exc).__name__}: {exc}"}
 
     if out is not None and args.batched_steps > 0 and world == 1:
         try:

@@ -255,7 +255,8 @@ fbsde_status fbsde_graph_destroy(fbsde_graph* graph);
  *
  * fbsde_group_autotune: times `trial_steps` group steps (after one warm-up)
  * for each candidate split of the SMs (all SMs for every instance; SMs in
- * proportion to each instance's contraction work; half of the SMs each) on
+ * proportion to each instance's contraction work, and twice that; half and a
+ * quarter of the SMs each) on
  * scratch copies of theta (Adam moments zero, step 1), keeps the fastest
  * split in the contexts and writes each instance's cap to caps_out (n ints)
  * and the step time in ms to *ms_out (may be NULL).  Synchronises the group's

@@ -174,8 +174,8 @@ fbsde_status fbsde_group_autotune(fbsde_group* g, const float* const* theta, flo
         return FBSDE_ERR_OOM;
     }
     // candidate splits: every instance on all SMs; SMs in proportion to each
-    // instance's points x width^2 (its share of the contraction work); half
-    // of the SMs each
+    // instance's points x width^2 (its share of the contraction work), and
+    // twice that; half and a quarter of the SMs each
     std::vector<double> work(n);
     double total = 0;
     for (int i = 0; i < n; ++i) {
@@ -189,6 +189,10 @@ fbsde_status fbsde_group_autotune(fbsde_group* g, const float* const* theta, flo
     for (int i = 0; i < n; ++i) prop[i] = std::max(8, (int)std::lround(g->sms * work[i] / total));
     cands.push_back(prop);
     cands.push_back(std::vector<int>(n, std::max(1, g->sms / 2)));
+    cands.push_back(std::vector<int>(n, std::max(1, g->sms / 4)));
+    std::vector<int> prop2(n);
+    for (int i = 0; i < n; ++i) prop2[i] = std::min(g->sms, 2 * prop[i]);
+    cands.push_back(prop2);
     std::vector<int> saved(n);
     for (int i = 0; i < n; ++i) saved[i] = g->ctx[i]->grid_cap;
     cudaEvent_t e0 = nullptr, e1 = nullptr;
