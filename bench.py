@@ -586,8 +586,8 @@ def main():
         del sa
         out["multilevel"] = multilevel_run(P, w, target, args.accuracy_steps)
 
-    # the stable network of the paper (NAIS-Net, HJB, Section 4): BF16 and FP32
-    # forms, through the layered tensor-core path
+    # the stable network of the paper (NAIS-Net, HJB, Section 4): BF16 form
+    # (fused per-tile kernels) and FP32 form
     if out is not None and args.nais_steps > 0:
         try:
             wn = P.workloads.WORKLOADS["hjb_d100_n64_m8192_nais6x256_tanh"]

@@ -162,9 +162,8 @@ fbsde_status fbsde_create(const fbsde_problem* problem, const fbsde_arch* arch, 
     add(Pm);                   // residuals r_n
     add(2 * (size_t)c->M);     // path_loss (double)
     if (c->akind == FBSDE_NAIS) { add(2 * L * w * w); }
-    add(w * w);                // sym
     add(c->part_floats);
-    add(32); add(16); add(16); // dscal, fscal, nonfinite
+    add(32); add(kMaxDepth + 1); add(16); // dscal, fscal, nonfinite
     add(c->pl.total);          // gradient buffer of train_step
     if (c->prec == FBSDE_FP32) add(fp32_workspace_floats(c));
     c->arena_bytes = total * sizeof(float);
@@ -188,10 +187,9 @@ fbsde_status fbsde_create(const fbsde_problem* problem, const fbsde_arch* arch, 
     c->path_loss_d = (double*)take(2 * (size_t)c->M);
     if (c->akind == FBSDE_NAIS)
         for (int l = 1; l <= c->L; ++l) { c->Amat[l] = take(w * w); c->gA[l] = take(w * w); }
-    c->sym = take(w * w);
     c->part = take(c->part_floats);
     c->dscal = (double*)take(32);
-    c->fscal = take(16);
+    c->fscal = take(kMaxDepth + 1);
     c->nonfinite = (int*)take(16);
     c->gradbuf = take(c->pl.total);
     if (c->prec == FBSDE_FP32) fp32_carve(c, cur);

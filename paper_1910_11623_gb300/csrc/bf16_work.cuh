@@ -69,7 +69,7 @@ struct Bf16Work {
     CUtensorMap mWinx, mWinxT, mW[kMaxDepth + 1], mWT[kMaxDepth + 1], mBx[kMaxDepth + 1], mBxT[kMaxDepth + 1];
     // MN-major maps for the weight gradients (box {64, 64})
     CUtensorMap tX, tV, tH[kMaxDepth + 1], tE[kMaxDepth + 1], tHD[kMaxDepth + 1], tAB[kMaxDepth + 1];
-    // per-tile fused kernels (FC / ResNet, depth <= kFusedMaxDepth, D <= 256)
+    // per-tile fused kernels (FC / ResNet / NAIS-Net, depth <= kFusedMaxDepth, D <= 256)
     bool fused = false;
     CUtensorMap sHb, sHDb, sABb, sEb;  // layer stacks of the operands, box {64, 128, 1} (TMA stores)
     int grid = 0;          // persistent CTAs
@@ -77,7 +77,7 @@ struct Bf16Work {
     bf16* G = nullptr;     // g_l, l < L, per 128-row tile column-pair-major (written by the fused forward)
     size_t G_stride = 0;   // elements between consecutive g_l
     bf16* scratch = nullptr;  // per-CTA activation-derivative scratch
-    float* pvec = nullptr;    // [(L+3) x w] per-column parameters of the fused backward
+    float* pvec = nullptr;    // [(2L+3) x w] per-column parameters of the fused backward
     // FP8 hidden layers (prec FBSDE_FP8_HIDDEN): E4M3 copies of W_l (l >= 1),
     // [w x wp8] bytes, their maps (box {128, w}) and per-layer inverse scales
     bool f8 = false;

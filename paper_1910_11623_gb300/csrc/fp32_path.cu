@@ -90,20 +90,6 @@ struct EpiPartial {  // split-K partial sums part[z][row][col]
     }
 };
 
-struct EpiAmat {  // A = -R^T R - eps I
-    float* out; int w; float eps;
-    __device__ void operator()(int row, int col, float acc, int) const {
-        out[(size_t)row * w + col] = -acc - (row == col ? eps : 0.f);
-    }
-};
-
-struct EpiNeg {
-    float* out; int ld;
-    __device__ void operator()(int row, int col, float acc, int) const {
-        out[(size_t)row * ld + col] = -acc;
-    }
-};
-
 // ---------------------------------------------------------------- small kernels
 
 // g_L = w_o (broadcast), e_L = c_L act'(a_L) w_o
@@ -159,16 +145,79 @@ __global__ void k_ones_t(size_t P, int M, float dt, float* __restrict__ ot) {
     ot[2 * p + 1] = (float)(p / M) * dt;
 }
 
-__global__ void k_sym(int w, const float* __restrict__ g, float* __restrict__ s) {
-    int i = blockIdx.x * blockDim.x + threadIdx.x;
-    if (i >= w * w) return;
-    const int r = i / w, c = i % w;
-    s[i] = g[(size_t)r * w + c] + g[(size_t)c * w + r];
+
+
+
+// w x w products of every NAIS-Net block in one launch (blockIdx.z = block
+// l - 1), 32 x 32 outputs per CTA, each of the 256 threads 2 x 2 of them:
+//   MODE 0: C_l = -X_l^T Y_l - eps I   (A_l = -R_l^T R_l - eps I)
+//   MODE 1: C_l =  X_l^T Y_l           (R_l^T R_l for the projection)
+//   MODE 2: C_l = -X_l (Y_l + Y_l^T)   (d loss / d R_l = -R_l (dA_l + dA_l^T))
+struct WxwArgs {
+    const float* X[kMaxDepth + 1];
+    const float* Y[kMaxDepth + 1];
+    float* C[kMaxDepth + 1];
+    int w;
+};
+
+template <int MODE>
+__global__ void __launch_bounds__(256) k_wxw(const WxwArgs a, float eps) {
+    const int l = blockIdx.z + 1, w = a.w;
+    const float* __restrict__ X = a.X[l];
+    const float* __restrict__ Y = a.Y[l];
+    __shared__ float xs[32][33];  // xs[k][m]
+    __shared__ float ys[32][33];  // ys[k][n]
+    const int tx = threadIdx.x & 15, ty = threadIdx.x >> 4;
+    const int m0 = blockIdx.y * 32, n0 = blockIdx.x * 32;
+    float acc[2][2] = {{0.f, 0.f}, {0.f, 0.f}};
+    for (int k0 = 0; k0 < w; k0 += 32) {
+        for (int i = threadIdx.x; i < 1024; i += 256) {
+            const int r = i >> 5, q = i & 31;
+            if (MODE == 2) {  // X[m][k]
+                const int m = m0 + r, k = k0 + q;
+                xs[q][r] = (m < w && k < w) ? X[(size_t)m * w + k] : 0.f;
+            } else {          // X[k][m]
+                const int k = k0 + r, m = m0 + q;
+                xs[r][q] = (m < w && k < w) ? X[(size_t)k * w + m] : 0.f;
+            }
+            const int k = k0 + r, n = n0 + q;
+            float yv = 0.f;
+            if (k < w && n < w) {
+                yv = Y[(size_t)k * w + n];
+                if (MODE == 2) yv += Y[(size_t)n * w + k];
+            }
+            ys[r][q] = yv;
+        }
+        __syncthreads();
+#pragma unroll 8
+        for (int kk = 0; kk < 32; ++kk) {
+            const float x0 = xs[kk][ty * 2], x1 = xs[kk][ty * 2 + 1];
+            const float y0 = ys[kk][tx * 2], y1 = ys[kk][tx * 2 + 1];
+            acc[0][0] = fmaf(x0, y0, acc[0][0]);
+            acc[0][1] = fmaf(x0, y1, acc[0][1]);
+            acc[1][0] = fmaf(x1, y0, acc[1][0]);
+            acc[1][1] = fmaf(x1, y1, acc[1][1]);
+        }
+        __syncthreads();
+    }
+#pragma unroll
+    for (int i = 0; i < 2; ++i)
+#pragma unroll
+        for (int j = 0; j < 2; ++j) {
+            const int m = m0 + ty * 2 + i, n = n0 + tx * 2 + j;
+            if (m >= w || n >= w) continue;
+            float v = acc[i][j];
+            if (MODE == 0) v = -v - (m == n ? eps : 0.f);
+            if (MODE == 2) v = -v;
+            a.C[l][(size_t)m * w + n] = v;
+        }
 }
 
-// ||G||_F^2 in one block (fixed order), then scale = sqrt(delta / ||G||_F) if
-// the norm exceeds delta, else 1.
-__global__ void k_proj_scale(int n, const float* __restrict__ G, float delta, float* __restrict__ scale) {
+// Per block l (one CTA each): ||C_l||_F^2 in a fixed order, then
+// scale[l] = sqrt(delta / ||C_l||_F) if the norm exceeds delta, else 1.
+__global__ void k_proj_scales(int n, const WxwArgs a, float delta, float* __restrict__ scale) {
+    const int l = blockIdx.x + 1;
+    const float* __restrict__ G = a.C[l];
     __shared__ double sh[1024];
     double acc = 0.0;
     for (int i = threadIdx.x; i < n; i += blockDim.x) acc += (double)G[i] * (double)G[i];
@@ -180,13 +229,15 @@ __global__ void k_proj_scale(int n, const float* __restrict__ G, float delta, fl
     }
     if (threadIdx.x == 0) {
         const double nrm = sqrt(sh[0]);
-        *scale = nrm > (double)delta ? (float)sqrt((double)delta / nrm) : 1.f;
+        scale[l] = nrm > (double)delta ? (float)sqrt((double)delta / nrm) : 1.f;
     }
 }
 
-__global__ void k_scale(int n, float* __restrict__ x, const float* __restrict__ scale) {
-    int i = blockIdx.x * blockDim.x + threadIdx.x;
-    if (i < n) x[i] *= *scale;
+// R_l *= scale[l] for every block (blockIdx.y = l - 1); R_l passed in Y.
+__global__ void k_scale_blocks(int n, const WxwArgs a, const float* __restrict__ scale) {
+    const int l = blockIdx.y + 1;
+    const int i = blockIdx.x * blockDim.x + threadIdx.x;
+    if (i < n) const_cast<float*>(a.Y[l])[i] *= scale[l];
 }
 
 __global__ void k_check_finite(size_t n, const float* __restrict__ x, int* __restrict__ flag) {
@@ -232,16 +283,28 @@ void fp32_carve(fbsde_ctx* c, float*& cur) {
     }
 }
 
-// NAIS: A_l = -R_l^T R_l - eps I for every block (Section 3.1).
-static fbsde_status form_nais_A(fbsde_ctx* c, const float* theta) {
-    for (int l = 1; l <= c->L; ++l) {
-        const float* R = theta + c->pl.W[l];
-        GemmArgs g{};
-        g.npairs = 1; g.Mrows = c->w; g.Ncols = c->w; g.kchunk = 1 << 30;
-        g.pair[0] = {R, R, c->w, c->w, c->w};
-        GEMM_LAUNCH(c, PROF_OTHER, true, true, g, 1, (EpiAmat{c->Amat[l], c->w, (float)c->eps}));
-    }
+static fbsde_status launch_wxw(fbsde_ctx* c, int mode, const WxwArgs& a, int cls) {
+    const int w = c->w, nt = (w + 31) / 32;
+    if (c->L < 1) return FBSDE_OK;
+    const dim3 grid(nt, nt, c->L);
+    const int tok = prof_begin(c, cls);
+    if (mode == 0) k_wxw<0><<<grid, 256, 0, c->stream>>>(a, (float)c->eps);
+    else if (mode == 1) k_wxw<1><<<grid, 256, 0, c->stream>>>(a, 0.f);
+    else k_wxw<2><<<grid, 256, 0, c->stream>>>(a, 0.f);
+    prof_end(c, cls, tok, 2.0 * w * (double)w * w * c->L);
+    FBSDE_CK_LAUNCH(c);
     return FBSDE_OK;
+}
+
+// NAIS: A_l = -R_l^T R_l - eps I for every block (Section 3.1), one launch.
+static fbsde_status form_nais_A(fbsde_ctx* c, const float* theta) {
+    WxwArgs a{};
+    a.w = c->w;
+    for (int l = 1; l <= c->L; ++l) {
+        a.X[l] = a.Y[l] = theta + c->pl.W[l];
+        a.C[l] = c->Amat[l];
+    }
+    return launch_wxw(c, 0, a, PROF_OTHER);
 }
 
 fbsde_status fp32_prepare_weights(fbsde_ctx* c, const float* theta) {
@@ -286,16 +349,17 @@ fbsde_status launch_rowdot(fbsde_ctx* c, const float* h, const float* theta, flo
     return FBSDE_OK;
 }
 
-// d loss / d R_l = -R_l (dA_l + dA_l^T) from the gradient dA_l in c->gA[l].
-fbsde_status nais_chain_R(fbsde_ctx* c, const float* theta, float* grad, int l) {
-    const int w = c->w;
-    k_sym<<<nblk((size_t)w * w, 256), 256, 0, c->stream>>>(w, c->gA[l], c->sym);
-    FBSDE_CK_LAUNCH(c);
-    GemmArgs gr{};
-    gr.npairs = 1; gr.Mrows = w; gr.Ncols = w; gr.kchunk = 1 << 30;
-    gr.pair[0] = {theta + c->pl.W[l], c->sym, w, w, w};
-    GEMM_LAUNCH(c, PROF_WGRAD, false, true, gr, 1, (EpiNeg{grad + c->pl.W[l], w}));
-    return FBSDE_OK;
+// d loss / d R_l = -R_l (dA_l + dA_l^T) from the gradients dA_l in c->gA[l],
+// every block in one launch.
+fbsde_status nais_chain_R(fbsde_ctx* c, const float* theta, float* grad) {
+    WxwArgs a{};
+    a.w = c->w;
+    for (int l = 1; l <= c->L; ++l) {
+        a.X[l] = theta + c->pl.W[l];
+        a.Y[l] = c->gA[l];
+        a.C[l] = grad + c->pl.W[l];
+    }
+    return launch_wxw(c, 2, a, PROF_WGRAD);
 }
 
 fbsde_status launch_check_finite(fbsde_ctx* c, const float* x, size_t n) {
@@ -431,15 +495,9 @@ fbsde_status fp32_backward(fbsde_ctx* c, const float* theta, float* grad) {
             gx.pair[0] = {f.AB[l], c->X, Pi, w, D};
             gx.pair[1] = {f.E[l], c->V, Pi, w, D};
             FBSDE_TRY(tn_reduce(c, gx, 0, D, grad + pl.B[l], K0, 1));
-            // dR = -R (dA + dA^T)
-            k_sym<<<nblk((size_t)w * w, 256), 256, 0, st>>>(w, c->gA[l], c->sym);
-            FBSDE_CK_LAUNCH(c);
-            GemmArgs gr{};
-            gr.npairs = 1; gr.Mrows = w; gr.Ncols = w; gr.kchunk = NOSPLIT;
-            gr.pair[0] = {theta + pl.W[l], c->sym, w, w, w};
-            GEMM_LAUNCH(c, PROF_WGRAD, false, true, gr, 1, (EpiNeg{grad + pl.W[l], w}));
         }
     }
+    if (c->akind == FBSDE_NAIS) FBSDE_TRY(nais_chain_R(c, theta, grad));  // dR = -R (dA + dA^T)
     {
         GemmArgs g{};
         g.npairs = 2; g.Mrows = w; g.Ncols = D;
@@ -474,18 +532,20 @@ fbsde_status fp32_backward(fbsde_ctx* c, const float* theta, float* grad) {
 // After an update: if ||R_l^T R_l||_F > delta, R_l *= sqrt(delta / ||R_l^T R_l||_F)
 // (Section 3.1: projection onto the feasible set of the Frobenius-norm bound).
 fbsde_status nais_project(fbsde_ctx* c, float* theta) {
-    const int w = c->w;
-    for (int l = 1; l <= c->L; ++l) {
-        float* R = theta + c->pl.W[l];
-        GemmArgs g{};
-        g.npairs = 1; g.Mrows = w; g.Ncols = w; g.kchunk = 1 << 30;
-        g.pair[0] = {R, R, w, w, w};
-        GEMM_LAUNCH(c, PROF_OTHER, true, true, g, 1, (EpiStore{c->sym, w}));
-        k_proj_scale<<<1, 1024, 0, c->stream>>>(w * w, c->sym, (float)c->delta, c->fscal);
-        FBSDE_CK_LAUNCH(c);
-        k_scale<<<nblk((size_t)w * w, 256), 256, 0, c->stream>>>(w * w, R, c->fscal);
-        FBSDE_CK_LAUNCH(c);
+    const int w = c->w, L = c->L;
+    if (L < 1) return FBSDE_OK;
+    // S_l = R_l^T R_l into the dA_l buffers (free once the update is done)
+    WxwArgs a{};
+    a.w = w;
+    for (int l = 1; l <= L; ++l) {
+        a.X[l] = a.Y[l] = theta + c->pl.W[l];
+        a.C[l] = c->gA[l];
     }
+    FBSDE_TRY(launch_wxw(c, 1, a, PROF_OTHER));
+    k_proj_scales<<<L, 1024, 0, c->stream>>>(w * w, a, (float)c->delta, c->fscal);
+    FBSDE_CK_LAUNCH(c);
+    k_scale_blocks<<<dim3(nblk((size_t)w * w, 256), L), 256, 0, c->stream>>>(w * w, a, c->fscal);
+    FBSDE_CK_LAUNCH(c);
     return FBSDE_OK;
 }
 

@@ -79,6 +79,19 @@ struct FGemm {
     int dcol = 0;        // TMEM column of the accumulator
     int acc = 0;         // 1: add to the accumulator's contents (a residual kept there)
     int f8 = 0;          // 1: E4M3 operands (K slices of 128, K = 32 per instruction)
+    // NAIS-Net blocks: after the nk slices over the tile, nx slices of 64 over
+    // the network input.  Each takes two ring stages: the weight slice (map
+    // wx, N rows) and then the BF16 input rows of this tile (map xa; with
+    // `dual`, map xb beside them at +16 KB for the second accumulator).
+    int nx = 0, Kx = 0;
+    const CUtensorMap* wx = nullptr;
+    const CUtensorMap* xa = nullptr;
+    const CUtensorMap* xb = nullptr;
+    // then a second contraction of the same tile (NAIS-Net: B_l[:,1:]^T e_l
+    // into the Z accumulator): nk2 weight slices of map2, N2 output columns
+    // at TMEM column dcol2, added to its contents when acc2
+    const CUtensorMap* map2 = nullptr;
+    int nk2 = 0, N2 = 0, dcol2 = 0, acc2 = 0;
 };
 
 // ---------------------------------------------------------------- small helpers
@@ -327,29 +340,35 @@ struct StoreSync {
 };
 
 // Per-layer vectors staged in shared memory once per CTA:
-// [l * w] bias of layer l (l = 0: b_in), [(L+1) w] w_o, [(L+2) w] W_in[:, 0].
+// [l * w] bias of layer l (l = 0: b_in; NAIS-Net: C_l), [(L+1) w] w_o,
+// [(L+2) w] W_in[:, 0], and for NAIS-Net [(L+2+l) w] B_l[:, 0], l = 1..L
+// (the weights of t, which enters every block).
 struct ParamOffsets {
-    unsigned long long bin, Win, wo, bo, b[kFusedMaxDepth + 1];
+    unsigned long long bin, Win, wo, bo, b[kFusedMaxDepth + 1], B[kFusedMaxDepth + 1];
+    int nais;
 };
+
+__host__ __device__ __forceinline__ int param_rows(int L, int nais) { return nais ? 2 * L + 3 : L + 3; }
+
+__device__ __forceinline__ float param_value(const float* th, const ParamOffsets& o, int L, int l, int c, int K0) {
+    if (l <= L) return th[(l == 0 ? o.bin : o.b[l]) + c];
+    if (l == L + 1) return th[o.wo + c];
+    if (l == L + 2) return th[o.Win + (size_t)c * K0];
+    return th[o.B[l - (L + 2)] + (size_t)c * K0];
+}
 
 __device__ __forceinline__ void stage_params(float* ptab, const float* th, const ParamOffsets& o, int L, int w,
                                              int K0) {
-    const int n = (L + 3) * w;
-    for (int i = threadIdx.x; i < n; i += blockDim.x) {
-        const int l = i / w, c = i % w;
-        float v;
-        if (l <= L) v = th[(l == 0 ? o.bin : o.b[l]) + c];
-        else if (l == L + 1) v = th[o.wo + c];
-        else v = th[o.Win + (size_t)c * K0];
-        ptab[i] = v;
-    }
+    const int n = param_rows(L, o.nais) * w;
+    for (int i = threadIdx.x; i < n; i += blockDim.x) ptab[i] = param_value(th, o, L, i / w, i % w, K0);
 }
 
 // ---------------------------------------------------------------- producer / MMA roles
 
 // Warp 0, one lane: stream the weight slices of every contraction of every
 // tile of this CTA through the ring.
-template <class Sched>
+// XS: the schedule may contain input slices (FGemm::nx).
+template <bool XS, class Sched>
 __device__ void producer_role(const Sched& sch, int ntiles, int nstages, uint8_t* ring, uint64_t* bfull,
                               uint64_t* bempty, volatile int* abort_flag, int* err) {
     int it = 0;
@@ -357,15 +376,29 @@ __device__ void producer_role(const Sched& sch, int ntiles, int nstages, uint8_t
     for (int t = blockIdx.x; t < ntiles && ok; t += gridDim.x) {
         for (int q = 0; q < sch.nq() && ok; ++q) {
             const FGemm g = sch.gemm(q);
-            for (int kc = 0; kc < g.nk; ++kc, ++it) {
+            const int nload = XS ? g.nk + 2 * g.nx + g.nk2 : g.nk;
+            for (int kc = 0; kc < nload; ++kc, ++it) {
                 const int s = it % nstages;
                 const uint32_t ph = (uint32_t)(it / nstages) & 1u;
                 if (*abort_flag || !tc::mbar_wait(&bempty[s], ph ^ 1u, tc::kWaitBudget)) {
                     ok = false;
                     break;
                 }
-                tc::mbar_expect_tx(&bfull[s], (uint32_t)g.N * 128u);
-                tc::tma_load_2d(ring + s * kFStageBytes, g.map, &bfull[s], kc * 64, 0);
+                if (!XS || kc < g.nk) {
+                    tc::mbar_expect_tx(&bfull[s], (uint32_t)g.N * 128u);
+                    tc::tma_load_2d(ring + s * kFStageBytes, g.map, &bfull[s], kc * 64, 0);
+                } else if (kc >= g.nk + 2 * g.nx) {
+                    tc::mbar_expect_tx(&bfull[s], (uint32_t)g.N2 * 128u);
+                    tc::tma_load_2d(ring + s * kFStageBytes, g.map2, &bfull[s], (kc - g.nk - 2 * g.nx) * 64, 0);
+                } else if (((kc - g.nk) & 1) == 0) {
+                    tc::mbar_expect_tx(&bfull[s], (uint32_t)g.N * 128u);
+                    tc::tma_load_2d(ring + s * kFStageBytes, g.wx, &bfull[s], ((kc - g.nk) >> 1) * 64, 0);
+                } else {
+                    const int x = ((kc - g.nk) >> 1) * 64;
+                    tc::mbar_expect_tx(&bfull[s], g.xb ? 32768u : 16384u);
+                    tc::tma_load_2d(ring + s * kFStageBytes, g.xa, &bfull[s], x, t * 128);
+                    if (g.xb) tc::tma_load_2d(ring + s * kFStageBytes + 16384, g.xb, &bfull[s], x, t * 128);
+                }
             }
         }
     }
@@ -380,7 +413,7 @@ __device__ void producer_role(const Sched& sch, int ntiles, int nstages, uint8_t
 // signalling the accumulator.
 // F8: the schedule may contain E4M3 contractions (FGemm::f8); without it
 // the loop is the BF16 one only.
-template <bool F8, class Sched>
+template <bool F8, bool XS, class Sched>
 __device__ void mma_role(const Sched& sch, int ntiles, int nstages, uint32_t abase0, uint32_t abase1,
                          uint32_t rbase, uint32_t tmem, uint64_t* bfull, uint64_t* bempty, uint64_t* accf,
                          uint64_t* aready, volatile int* abort_flag, int* err) {
@@ -425,6 +458,46 @@ __device__ void mma_role(const Sched& sch, int ntiles, int nstages, uint32_t aba
                 }
                 tc::mma_commit(&bempty[s]);
             }
+            // input slices: weights in one stage, the input rows in the next;
+            // both accumulate onto the tile's contraction
+            for (int j = 0; XS && ok && j < g.nx; ++j, it += 2) {
+                const int s1 = it % nstages, s2 = (it + 1) % nstages;
+                if (*abort_flag || !tc::mbar_wait(&bfull[s1], (uint32_t)(it / nstages) & 1u, tc::kWaitBudget) ||
+                    !tc::mbar_wait(&bfull[s2], (uint32_t)((it + 1) / nstages) & 1u, tc::kWaitBudget)) {
+                    ok = false;
+                    break;
+                }
+                tc::tc_fence_after();
+                const int nsteps = min(4, (g.Kx - j * 64 + 15) / 16);
+                for (int k = 0; k < nsteps; ++k) {
+                    const uint64_t bd = tc::sdesc_sw128(rbase + (uint32_t)s1 * kFStageBytes + 32u * k, 16u);
+                    const uint64_t ad = tc::sdesc_sw128(rbase + (uint32_t)s2 * kFStageBytes + 32u * k, 16u);
+                    tc::mma_bf16(tmem + (uint32_t)g.dcol, ad, bd, idesc, 1u);
+                    if (dual) {
+                        const uint64_t ad1 = tc::sdesc_sw128(rbase + (uint32_t)s2 * kFStageBytes + 16384u + 32u * k, 16u);
+                        tc::mma_bf16(tmem + 256u, ad1, bd, idesc, 1u);
+                    }
+                }
+                tc::mma_commit(&bempty[s1]);
+                tc::mma_commit(&bempty[s2]);
+            }
+            // second contraction of the tile
+            for (int kc = 0; XS && ok && kc < g.nk2; ++kc, ++it) {
+                const int s = it % nstages;
+                if (*abort_flag || !tc::mbar_wait(&bfull[s], (uint32_t)(it / nstages) & 1u, tc::kWaitBudget)) {
+                    ok = false;
+                    break;
+                }
+                tc::tc_fence_after();
+                const uint32_t idesc2 = tc::idesc_bf16(128, g.N2, 0, 0);
+                const int nsteps = min(4, (g.K - kc * 64 + 15) / 16);
+                for (int k = 0; k < nsteps; ++k) {
+                    const uint64_t ad = tc::sdesc_sw128(abase + (uint32_t)kc * 16384u + 32u * k, 16u);
+                    const uint64_t bd = tc::sdesc_sw128(rbase + (uint32_t)s * kFStageBytes + 32u * k, 16u);
+                    tc::mma_bf16(tmem + (uint32_t)g.dcol2, ad, bd, idesc2, (g.acc2 || kc > 0 || k > 0) ? 1u : 0u);
+                }
+                tc::mma_commit(&bempty[s]);
+            }
             if (ok) tc::mma_commit(accf);
         }
     }
@@ -458,6 +531,11 @@ struct FwdZArgs {
     int f8;
     CUtensorMap wf8[kFusedMaxDepth + 1];
     const float* f8inv;
+    // NAIS-Net: B_l[:, 1:] (box {64, w}), streamed beside the X rows, its
+    // transpose (box {64, Dn}) for the Z terms, and the step h
+    CUtensorMap wbx[kFusedMaxDepth + 1];
+    CUtensorMap wbxT[kFusedMaxDepth + 1];
+    float hs;
 };
 
 struct FwdZSched {
@@ -471,9 +549,24 @@ struct FwdZSched {
         g.dual = 0;
         if (q == 0) { g.map = &a->wf[0]; g.nk = a->Dp / 64; g.K = a->D; g.N = a->w; }
         else if (q <= L && a->f8) { g.map = &a->wf8[q]; g.nk = (a->w + 127) / 128; g.K = a->w; g.N = a->w; g.f8 = 1; }
-        else if (q <= L) { g.map = &a->wf[q]; g.nk = a->wp / 64; g.K = a->w; g.N = a->w; }
-        else if (q <= 2 * L) { g.map = &a->wr[2 * L + 1 - q]; g.nk = a->wp / 64; g.K = a->w; g.N = a->w; }
-        else { g.map = &a->wr[0]; g.nk = a->wp / 64; g.K = a->w; g.N = a->Dn; }
+        else if (q <= L) {
+            g.map = &a->wf[q]; g.nk = a->wp / 64; g.K = a->w; g.N = a->w;
+            if (a->off.nais) { g.nx = a->Dp / 64; g.Kx = a->D; g.wx = &a->wbx[q]; g.xa = &a->xin; }
+        }
+        else if (q <= 2 * L) {
+            const int l = 2 * L + 1 - q;
+            g.map = &a->wr[l]; g.nk = a->wp / 64; g.K = a->w; g.N = a->w;
+            if (a->off.nais) {
+                // g_{l-1} = g_l + A_l^T e_l accumulates in place (columns 0..),
+                // Z += B_l[:,1:]^T e_l in columns 256..
+                g.acc = 1;
+                g.map2 = &a->wbxT[l]; g.nk2 = a->wp / 64; g.N2 = a->Dn; g.dcol2 = 256; g.acc2 = l < L;
+            }
+        }
+        else {
+            g.map = &a->wr[0]; g.nk = a->wp / 64; g.K = a->w; g.N = a->Dn;
+            if (a->off.nais) { g.dcol = 256; g.acc = L > 0; }
+        }
         return g;
     }
     // into L2 while contraction q runs: the act' block its epilogue reads
@@ -487,7 +580,8 @@ struct FwdZSched {
     }
 };
 
-template <int ACT, bool RES, bool F8>
+// NAIS: NAIS-Net blocks (h_l = h_{l-1} + h act(A_l h_{l-1} + B_l u + C_l), Section 3.1)
+template <int ACT, bool RES, bool F8, bool NAIS>
 __global__ void __launch_bounds__(fused_threads(kFwdGroups), 1) k_fused_fwdz(const __grid_constant__ FwdZArgs a) {
     constexpr int NG = kFwdGroups, NE = 128 * NG;
     extern __shared__ uint8_t smem_raw[];
@@ -495,7 +589,8 @@ __global__ void __launch_bounds__(fused_threads(kFwdGroups), 1) k_fused_fwdz(con
     uint8_t* tile = smem;
     uint8_t* ring = smem + kFTileBytes;
     float* ptab = (float*)(ring + kFwdStages * kFStageBytes);
-    uint64_t* bfull = (uint64_t*)(ptab + (a.L + 3) * a.w);
+    const int prows = param_rows(a.L, NAIS);
+    uint64_t* bfull = (uint64_t*)(ptab + prows * a.w);
     uint64_t* bempty = bfull + kFwdStages;
     uint64_t* accf = bempty + kFwdStages;
     uint64_t* aready = accf + 1;
@@ -505,7 +600,7 @@ __global__ void __launch_bounds__(fused_threads(kFwdGroups), 1) k_fused_fwdz(con
     uint64_t* ybar = xfull + 1;
     uint32_t* tslot = (uint32_t*)(ybar + 1);
     volatile int* abort_flag = (volatile int*)(tslot + 1);
-    float* ysum = (float*)(smem + kFTileBytes + kFwdStages * kFStageBytes) + (a.L + 3) * a.w + 64;
+    float* ysum = (float*)(smem + kFTileBytes + kFwdStages * kFStageBytes) + prows * a.w + 64;
 
     const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
     const int L = a.L;
@@ -536,10 +631,10 @@ __global__ void __launch_bounds__(fused_threads(kFwdGroups), 1) k_fused_fwdz(con
     const uint32_t tmem = *tslot;
 
     if (warp == 0) {
-        if (lane == 0) producer_role(sch, a.ntiles, kFwdStages, ring, bfull, bempty, abort_flag, a.err);
+        if (lane == 0) producer_role<NAIS>(sch, a.ntiles, kFwdStages, ring, bfull, bempty, abort_flag, a.err);
     } else if (warp == 1) {
         if (lane == 0)
-            mma_role<F8>(sch, a.ntiles, kFwdStages, tc::smem_u32(tile), tc::smem_u32(tile), tc::smem_u32(ring), tmem,
+            mma_role<F8, NAIS>(sch, a.ntiles, kFwdStages, tc::smem_u32(tile), tc::smem_u32(tile), tc::smem_u32(ring), tmem,
                      bfull, bempty, accf, aready, abort_flag, a.err);
     } else {
         const int eg = (warp - 2) >> 2;  // epilogue group: chunks eg, eg + NG, ...
@@ -602,6 +697,8 @@ __global__ void __launch_bounds__(fused_threads(kFwdGroups), 1) k_fused_fwdz(con
                     // forward layer l: a = acc + b_l (+ t W_in[:,0]); h_l = [h_{l-1}] + act(a)
                     const int l = q;
                     const float* bias = ptab + l * a.w;
+                    const float* bt = ptab + (L + 2 + l) * a.w;  // NAIS: B_l[:, 0]
+                    const bool blk_nais = NAIS && l >= 1;
                     uint32_t* sc = scr + (size_t)l * blk;
                     float ypart = 0.f;
                     // FP8 hidden layers: the accumulator of layer l >= 1 carries the
@@ -621,9 +718,10 @@ __global__ void __launch_bounds__(fused_threads(kFwdGroups), 1) k_fused_fwdz(con
                             float av = F8 ? fmaf(__uint_as_float(rv[j]), ascale, bias[c0 + j])
                                           : __uint_as_float(rv[j]) + bias[c0 + j];
                             if (l == 0) av = fmaf(tval, win0[c0 + j], av);
+                            if (blk_nais) av = fmaf(tval, bt[c0 + j], av);
                             const Act3 f = act3_sfu<ACT>(av);
-                            h[j] = ((RES && l >= 1) ? __uint_as_float(rr[j]) : 0.f) + f.f;
-                            d1[j] = f.d1;
+                            h[j] = ((RES && l >= 1) ? __uint_as_float(rr[j]) : 0.f) + (blk_nais ? a.hs * f.f : f.f);
+                            d1[j] = blk_nais ? a.hs * f.d1 : f.d1;
                         }
                         if (l < L) {
                             if (F8 && f8) st_tile8_e4m3(tile, row, c0, h, hscale);
@@ -639,6 +737,8 @@ __global__ void __launch_bounds__(fused_threads(kFwdGroups), 1) k_fused_fwdz(con
                                 e[j] = d1[j] * wo[c0 + j];
                             }
                             st_tile8(tile, row, c0, e);
+                            // NAIS-Net: g_L = w_o seeds the in-place accumulation of g
+                            if (NAIS) tmem_st_f8(tacc + (uint32_t)c0, wo + c0);
                         }
                     }
                     if (l == L) {
@@ -664,28 +764,31 @@ __global__ void __launch_bounds__(fused_threads(kFwdGroups), 1) k_fused_fwdz(con
                             const int c0 = ch * 8;
                             float d1[8];
                             unpack8(du, d1);
+                            // ResNet: g_l from the FP32 residual columns; NAIS-Net: the
+                            // contraction accumulated g_{l-1} in place
+                            constexpr bool RRES = RES && !NAIS;
                             uint32_t rv[8], rr[8];
                             tc::tmem_ld8(tacc + (uint32_t)c0, rv);
-                            if (RES && l < L) tc::tmem_ld8(tres + (uint32_t)c0, rr);
+                            if (RRES && l < L) tc::tmem_ld8(tres + (uint32_t)c0, rr);
                             tc::tmem_wait_ld();
                             float g[8], e[8];
 #pragma unroll
                             for (int j = 0; j < 8; ++j) {
-                                const float gl = RES ? (l == L ? wo[c0 + j] : __uint_as_float(rr[j])) : 0.f;
+                                const float gl = RRES ? (l == L ? wo[c0 + j] : __uint_as_float(rr[j])) : 0.f;
                                 g[j] = gl + __uint_as_float(rv[j]);
                                 e[j] = d1[j] * g[j];
                             }
                             if (a.for_grad) st_pm8h(gout, row, c0, g, pol_stream);
                             st_tile8(tile, row, c0, e);
-                            if (RES) tmem_st_f8(tres + (uint32_t)c0, g);
+                            if (RRES) tmem_st_f8(tres + (uint32_t)c0, g);
                         });
                     store_layer = l - 1;
                 } else {
-                    // Z = W_in[:,1:]^T e_0
+                    // Z = W_in[:,1:]^T e_0 (NAIS-Net: + sum_l B_l[:,1:]^T e_l, columns 256..)
                     for (int ch = eg; ch < a.Dn / 8; ch += NG) {
                         const int c0 = ch * 8;
                         uint32_t rv[8];
-                        tc::tmem_ld8(tacc + (uint32_t)c0, rv);
+                        tc::tmem_ld8(tacc + (NAIS ? 256u : 0u) + (uint32_t)c0, rv);
                         tc::tmem_wait_ld();
                         if (valid) {
                             float* zr = a.Z + (size_t)p * a.D + c0;
@@ -749,11 +852,13 @@ struct BwdArgs {
     bf16* HbL;                 // h_L rows of wp (its tile slot holds abar_L)
     uint32_t* scratch;         // per CTA: act'(a_l) and S_l, l < L, column-pair-major
     ParamOffsets off;
-    const float* pvec;  // [(L+3) x w]: b_0..b_L, w_o, W_in[:,0]
+    const float* pvec;  // [param_rows x w]: b_0..b_L, w_o, W_in[:,0] (NAIS-Net: B_l[:,0])
     int P, M, D, Dp, w, wp, L, ntiles;
-    int res;            // ResNet: hbar accumulates in place in TMEM columns 256..
+    int res;            // ResNet, NAIS-Net: hbar accumulates in place in TMEM columns 256..
     float dt;
     int* err;
+    CUtensorMap wbx[kFusedMaxDepth + 1];  // NAIS-Net: B_l[:, 1:] (box {64, w})
+    float hs;                             // NAIS-Net step h
 };
 
 struct BwdSched {
@@ -771,6 +876,10 @@ struct BwdSched {
             g.nk = (q == 0 ? a->Dp : a->wp) / 64;
             g.K = q == 0 ? a->D : a->w;
             g.N = a->w;
+            if (q > 0 && a->off.nais) {
+                // forward B_l x and tangent B_l v from the same weight slices
+                g.nx = a->Dp / 64; g.Kx = a->D; g.wx = &a->wbx[q]; g.xa = &a->xb; g.xb = &a->vb;
+            }
         } else {
             const int l = L - (q - (L + 1));
             g.asel = 0;
@@ -802,7 +911,7 @@ struct BwdSched {
 // The backward recomputes the forward with the BF16 skip path of the tile (the
 // FP32 residual of k_fused_fwdz has no room here: TMEM holds both the forward
 // and the tangent accumulators), and carries the tangent h' in BF16 as well.
-template <int ACT, bool RES>
+template <int ACT, bool RES, bool NAIS>
 __global__ void __launch_bounds__(bwd_threads(), 1) k_fused_bwd(const __grid_constant__ BwdArgs a) {
     constexpr int NG = kBwdGroups, NE = 128 * NG;
     extern __shared__ uint8_t smem_raw[];
@@ -811,7 +920,8 @@ __global__ void __launch_bounds__(bwd_threads(), 1) k_fused_bwd(const __grid_con
     uint8_t* tile_d = smem + kFTileBytes;    // h'_l
     uint8_t* ring = smem + 2 * kFTileBytes;
     float* ptab = (float*)(ring + kBwdStages * kFStageBytes);
-    uint64_t* bfull = (uint64_t*)(ptab + (a.L + 3) * a.w);
+    const int prows = param_rows(a.L, NAIS);
+    uint64_t* bfull = (uint64_t*)(ptab + prows * a.w);
     uint64_t* bempty = bfull + kBwdStages;
     uint64_t* accf = bempty + kBwdStages;
     uint64_t* aready = accf + 1;
@@ -825,7 +935,7 @@ __global__ void __launch_bounds__(bwd_threads(), 1) k_fused_bwd(const __grid_con
     const int L = a.L;
     const BwdSched sch{&a};
 
-    for (int k = threadIdx.x; k < (L + 3) * a.w / 4; k += blockDim.x)
+    for (int k = threadIdx.x; k < prows * a.w / 4; k += blockDim.x)
         reinterpret_cast<float4*>(ptab)[k] = __ldg(reinterpret_cast<const float4*>(a.pvec) + k);
     if (threadIdx.x == 0) {
         for (int s = 0; s < kBwdStages; ++s) {
@@ -852,10 +962,10 @@ __global__ void __launch_bounds__(bwd_threads(), 1) k_fused_bwd(const __grid_con
     if (warp < 4) {
         tc::setmaxnreg_dec<kBwdRegsCtl>();
         if (warp == 0) {
-            if (lane == 0) producer_role(sch, a.ntiles, kBwdStages, ring, bfull, bempty, abort_flag, a.err);
+            if (lane == 0) producer_role<NAIS>(sch, a.ntiles, kBwdStages, ring, bfull, bempty, abort_flag, a.err);
         } else if (warp == 1) {
             if (lane == 0)
-                mma_role<false>(sch, a.ntiles, kBwdStages, tc::smem_u32(tile_h), tc::smem_u32(tile_d), tc::smem_u32(ring),
+                mma_role<false, NAIS>(sch, a.ntiles, kBwdStages, tc::smem_u32(tile_h), tc::smem_u32(tile_d), tc::smem_u32(ring),
                          tmem, bfull, bempty, accf, aready, abort_flag, a.err);
         }
     } else {
@@ -929,6 +1039,8 @@ __global__ void __launch_bounds__(bwd_threads(), 1) k_fused_bwd(const __grid_con
                     // at the top (l = L) also abar_L = act'(a_L) alpha w_o + S_L and hbar_L = alpha w_o
                     const int l = q;
                     const float* bias = ptab + (size_t)l * a.w;
+                    const float* bt = ptab + (size_t)(L + 2 + l) * a.w;  // NAIS: B_l[:, 0]
+                    const bool blk_nais = NAIS && l >= 1;
                     const uint32_t* gin = gtile + (size_t)l * a.G_words;
                     auto loadt = [&](int ch, uint32_t (&r)[16]) {
                         tc::tmem_ld8(tacc + (uint32_t)(ch * 8), *reinterpret_cast<uint32_t(*)[8]>(r));
@@ -944,9 +1056,9 @@ __global__ void __launch_bounds__(bwd_threads(), 1) k_fused_bwd(const __grid_con
                             ld_tile8(tile_h, row, c0, hp);
                             ld_tile8(tile_d, row, c0, hdp);
                         }
-                        if (l == 0) {
+                        if (l == 0 || blk_nais) {
                             float w0[8];
-                            ld_f8(win0 + c0, w0);
+                            ld_f8((l == 0 ? win0 : bt) + c0, w0);
 #pragma unroll
                             for (int j = 0; j < 8; ++j) bv[j] = fmaf(tval, w0[j], bv[j]);
                         }
@@ -954,7 +1066,10 @@ __global__ void __launch_bounds__(bwd_threads(), 1) k_fused_bwd(const __grid_con
 #pragma unroll
                         for (int j = 0; j < 8; ++j) {
                             const float av = __uint_as_float(rt[j]) + bv[j];
-                            const Act3 f = act3_sfu<ACT>(av);
+                            Act3 f = act3_sfu<ACT>(av);
+                            if (blk_nais) {
+                                f.f *= a.hs; f.d1 *= a.hs; f.d2 *= a.hs;
+                            }
                             const float ad = __uint_as_float(rt[8 + j]);
                             h[j] = ((RES && l >= 1) ? hp[j] : 0.f) + f.f;
                             hd[j] = ((RES && l >= 1) ? hdp[j] : 0.f) + f.d1 * ad;
@@ -1057,12 +1172,12 @@ __global__ void __launch_bounds__(bwd_threads(), 1) k_fused_bwd(const __grid_con
 
 // ---------------------------------------------------------------- host launchers
 
-static size_t fwdz_smem_bytes(int L, int w) {
-    return 1024 + kFTileBytes + (size_t)kFwdStages * kFStageBytes + (size_t)(L + 3) * w * 4 + 256 +
+static size_t fwdz_smem_bytes(int L, int w, int nais) {
+    return 1024 + kFTileBytes + (size_t)kFwdStages * kFStageBytes + (size_t)param_rows(L, nais) * w * 4 + 256 +
            (size_t)kFwdGroups * 128 * 4 + 64;
 }
-static size_t bwd_smem_bytes(int L, int w) {
-    return 1024 + 2 * kFTileBytes + (size_t)kBwdStages * kFStageBytes + (size_t)(L + 3) * w * 4 + 128;
+static size_t bwd_smem_bytes(int L, int w, int nais) {
+    return 1024 + 2 * kFTileBytes + (size_t)kBwdStages * kFStageBytes + (size_t)param_rows(L, nais) * w * 4 + 128;
 }
 
 // `launch_regs` > 0: the kernel moves registers between warpgroups, which
@@ -1087,7 +1202,11 @@ static ParamOffsets param_offsets(const fbsde_ctx* c) {
     ParamOffsets o;
     std::memset(&o, 0, sizeof(o));
     o.bin = c->pl.bin; o.Win = c->pl.Win; o.wo = c->pl.wo; o.bo = c->pl.bo;
-    for (int l = 1; l <= c->L; ++l) o.b[l] = c->pl.b[l];
+    o.nais = c->akind == FBSDE_NAIS ? 1 : 0;
+    for (int l = 1; l <= c->L; ++l) {
+        o.b[l] = c->pl.b[l];
+        if (o.nais) o.B[l] = c->pl.B[l];
+    }
     return o;
 }
 
@@ -1114,30 +1233,40 @@ fbsde_status fused_forward(fbsde_ctx* c, const float* theta, bool for_grad) {
         for (int l = 1; l <= c->L; ++l) a.wf8[l] = b->mW8[l];
         a.f8inv = b->f8inv;
     }
+    const bool nais = c->akind == FBSDE_NAIS;
+    if (nais) {
+        for (int l = 1; l <= c->L; ++l) a.wbx[l] = b->mBx[l];
+        for (int l = 1; l <= c->L; ++l) a.wbxT[l] = b->mBxT[l];
+        a.hs = (float)c->h;
+    }
     const int cap = c->grid_cap > 0 && c->grid_cap < b->grid ? c->grid_cap : b->grid;
     const int grid = a.ntiles < cap ? a.ntiles : cap;
-    const size_t smem = fwdz_smem_bytes(c->L, c->w);
+    const size_t smem = fwdz_smem_bytes(c->L, c->w, nais ? 1 : 0);
     const int FT = fused_threads(kFwdGroups);
     const bool res = c->akind == FBSDE_RESNET;
     const int tok = prof_begin(c, PROF_POINTS);
     cudaError_t e;
-    if (b->f8) {
+    if (nais) {
+        e = c->act == FBSDE_TANH ? launch_fused(k_fused_fwdz<FBSDE_TANH, true, false, true>, a, grid, FT, smem, c->stream)
+                                 : launch_fused(k_fused_fwdz<FBSDE_SIN, true, false, true>, a, grid, FT, smem, c->stream);
+    } else if (b->f8) {
         if (c->act == FBSDE_TANH)
-            e = res ? launch_fused(k_fused_fwdz<FBSDE_TANH, true, true>, a, grid, FT, smem, c->stream)
-                    : launch_fused(k_fused_fwdz<FBSDE_TANH, false, true>, a, grid, FT, smem, c->stream);
+            e = res ? launch_fused(k_fused_fwdz<FBSDE_TANH, true, true, false>, a, grid, FT, smem, c->stream)
+                    : launch_fused(k_fused_fwdz<FBSDE_TANH, false, true, false>, a, grid, FT, smem, c->stream);
         else
-            e = res ? launch_fused(k_fused_fwdz<FBSDE_SIN, true, true>, a, grid, FT, smem, c->stream)
-                    : launch_fused(k_fused_fwdz<FBSDE_SIN, false, true>, a, grid, FT, smem, c->stream);
+            e = res ? launch_fused(k_fused_fwdz<FBSDE_SIN, true, true, false>, a, grid, FT, smem, c->stream)
+                    : launch_fused(k_fused_fwdz<FBSDE_SIN, false, true, false>, a, grid, FT, smem, c->stream);
     } else if (c->act == FBSDE_TANH) {
-        e = res ? launch_fused(k_fused_fwdz<FBSDE_TANH, true, false>, a, grid, FT, smem, c->stream)
-                : launch_fused(k_fused_fwdz<FBSDE_TANH, false, false>, a, grid, FT, smem, c->stream);
+        e = res ? launch_fused(k_fused_fwdz<FBSDE_TANH, true, false, false>, a, grid, FT, smem, c->stream)
+                : launch_fused(k_fused_fwdz<FBSDE_TANH, false, false, false>, a, grid, FT, smem, c->stream);
     } else {
-        e = res ? launch_fused(k_fused_fwdz<FBSDE_SIN, true, false>, a, grid, FT, smem, c->stream)
-                : launch_fused(k_fused_fwdz<FBSDE_SIN, false, false>, a, grid, FT, smem, c->stream);
+        e = res ? launch_fused(k_fused_fwdz<FBSDE_SIN, true, false, false>, a, grid, FT, smem, c->stream)
+                : launch_fused(k_fused_fwdz<FBSDE_SIN, false, false, false>, a, grid, FT, smem, c->stream);
     }
-    // algorithmic flops: lift + L layers forward, L reverse layers and the Z contraction
+    // algorithmic flops: lift + L layers forward (NAIS-Net: + B_l x), L reverse
+    // layers and the Z contraction
     const double P = a.P, w = a.w, D = a.D;
-    prof_end(c, PROF_POINTS, tok, 2.0 * P * w * (2.0 * D + 2.0 * c->L * w));
+    prof_end(c, PROF_POINTS, tok, 2.0 * P * w * (2.0 * D + 2.0 * c->L * w + (nais ? c->L * D : 0.0)));
     if (e != cudaSuccess) return set_err(c, FBSDE_ERR_CUDA, std::string("fused forward: ") + cudaGetErrorString(e));
     ++c->n_launch;
     return FBSDE_OK;
@@ -1147,15 +1276,9 @@ fbsde_status fused_forward(fbsde_ctx* c, const float* theta, bool for_grad) {
 // into one aligned table.
 __global__ void k_stage_pvec(const float* __restrict__ th, ParamOffsets o, int L, int w, int K0,
                              float* __restrict__ pvec) {
-    const int n = (L + 3) * w;
-    for (int i = blockIdx.x * blockDim.x + threadIdx.x; i < n; i += gridDim.x * blockDim.x) {
-        const int l = i / w, c = i % w;
-        float v;
-        if (l <= L) v = th[(l == 0 ? o.bin : o.b[l]) + c];
-        else if (l == L + 1) v = th[o.wo + c];
-        else v = th[o.Win + (size_t)c * K0];
-        pvec[i] = v;
-    }
+    const int n = param_rows(L, o.nais) * w;
+    for (int i = blockIdx.x * blockDim.x + threadIdx.x; i < n; i += gridDim.x * blockDim.x)
+        pvec[i] = param_value(th, o, L, i / w, i % w, K0);
 }
 
 fbsde_status fused_backward(fbsde_ctx* c, const float* theta) {
@@ -1176,7 +1299,12 @@ fbsde_status fused_backward(fbsde_ctx* c, const float* theta) {
     a.P = (int)c->P(); a.M = c->M; a.D = c->D; a.Dp = b->Dp; a.w = c->w; a.wp = b->wp;
     a.L = c->L; a.ntiles = (a.P + 127) / 128; a.dt = (float)(c->T / c->N); a.err = b->err;
     a.pvec = b->pvec;
-    a.res = c->akind == FBSDE_RESNET ? 1 : 0;
+    const bool nais = c->akind == FBSDE_NAIS;
+    a.res = c->akind != FBSDE_FC ? 1 : 0;
+    if (nais) {
+        for (int l = 1; l <= c->L; ++l) a.wbx[l] = b->mBx[l];
+        a.hs = (float)c->h;
+    }
     k_stage_pvec<<<4, 256, 0, c->stream>>>(theta, a.off, c->L, c->w, c->D + 1, b->pvec);
     {
         cudaError_t le = cudaGetLastError();
@@ -1185,21 +1313,24 @@ fbsde_status fused_backward(fbsde_ctx* c, const float* theta) {
     }
     const int cap = c->grid_cap > 0 && c->grid_cap < b->grid ? c->grid_cap : b->grid;
     const int grid = a.ntiles < cap ? a.ntiles : cap;
-    const size_t smem = bwd_smem_bytes(c->L, c->w);
+    const size_t smem = bwd_smem_bytes(c->L, c->w, nais ? 1 : 0);
     const int FT = bwd_threads(), R = kBwdRegsLaunch;
     const bool res = c->akind == FBSDE_RESNET;
     const int tok = prof_begin(c, PROF_POINTS);
     cudaError_t e;
-    if (c->act == FBSDE_TANH)
-        e = res ? launch_fused(k_fused_bwd<FBSDE_TANH, true>, a, grid, FT, smem, c->stream, R)
-                : launch_fused(k_fused_bwd<FBSDE_TANH, false>, a, grid, FT, smem, c->stream, R);
+    if (nais)
+        e = c->act == FBSDE_TANH ? launch_fused(k_fused_bwd<FBSDE_TANH, true, true>, a, grid, FT, smem, c->stream, R)
+                                 : launch_fused(k_fused_bwd<FBSDE_SIN, true, true>, a, grid, FT, smem, c->stream, R);
+    else if (c->act == FBSDE_TANH)
+        e = res ? launch_fused(k_fused_bwd<FBSDE_TANH, true, false>, a, grid, FT, smem, c->stream, R)
+                : launch_fused(k_fused_bwd<FBSDE_TANH, false, false>, a, grid, FT, smem, c->stream, R);
     else
-        e = res ? launch_fused(k_fused_bwd<FBSDE_SIN, true>, a, grid, FT, smem, c->stream, R)
-                : launch_fused(k_fused_bwd<FBSDE_SIN, false>, a, grid, FT, smem, c->stream, R);
-    // algorithmic flops: tangent (lift + L layers) and adjoint (L layers); the
-    // forward recomputation is overhead and not counted
+        e = res ? launch_fused(k_fused_bwd<FBSDE_SIN, true, false>, a, grid, FT, smem, c->stream, R)
+                : launch_fused(k_fused_bwd<FBSDE_SIN, false, false>, a, grid, FT, smem, c->stream, R);
+    // algorithmic flops: tangent (lift + L layers, NAIS-Net: + B_l v) and
+    // adjoint (L layers); the forward recomputation is overhead and not counted
     const double P = a.P, w = a.w, D = a.D;
-    prof_end(c, PROF_POINTS, tok, 2.0 * P * w * (D + 2.0 * c->L * w));
+    prof_end(c, PROF_POINTS, tok, 2.0 * P * w * (D + 2.0 * c->L * w + (nais ? c->L * D : 0.0)));
     if (e != cudaSuccess) return set_err(c, FBSDE_ERR_CUDA, std::string("fused backward: ") + cudaGetErrorString(e));
     ++c->n_launch;
     return FBSDE_OK;

@@ -97,7 +97,6 @@ struct fbsde_ctx {
     bool need_V32 = true;      // FP32 v_n consumed (FP32 form, layered BF16 sweeps)
     float* Amat[fbsde::kMaxDepth + 1] = {};  // NAIS A_l = -R^T R - eps I [w, w]
     float* gA[fbsde::kMaxDepth + 1] = {};    // NAIS d loss / d A_l       [w, w]
-    float* sym = nullptr;      // NAIS scratch [w, w]
     float* part = nullptr;     // split-K partial sums
     size_t part_floats = 0;
     double* dscal = nullptr;   // device scalars (loss accumulators, norms)
@@ -189,7 +188,7 @@ fbsde_status bf16_backward(fbsde_ctx* ctx, const float* theta, float* grad);
 
 // Helpers of the FP32 form reused by the BF16 form.
 fbsde_status launch_rowdot(fbsde_ctx* c, const float* h, const float* theta, float* y);
-fbsde_status nais_chain_R(fbsde_ctx* c, const float* theta, float* grad, int l);
+fbsde_status nais_chain_R(fbsde_ctx* c, const float* theta, float* grad);
 fbsde_status launch_check_finite(fbsde_ctx* c, const float* x, size_t n);
 
 // Skip s and scale c of layer l in h_l = s h_{l-1} + c act(a_l): (0, 1) for

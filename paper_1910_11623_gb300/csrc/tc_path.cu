@@ -102,13 +102,13 @@ fbsde_status bf16_create(fbsde_ctx* c) {
     const size_t Pm = c->Pmax();
     b->OP_stride = rup(Pm * b->wp, 128);
     const size_t nl = (size_t)L + 1;
-    // per-tile fused kernels: FC / ResNet, depth <= kFusedMaxDepth, D <= 256
+    // per-tile fused kernels: FC / ResNet / NAIS-Net, depth <= kFusedMaxDepth, D <= 256
     if (b->Dn > 256)
         return set_err(c, FBSDE_ERR_UNSUPPORTED,
                        "the BF16 forms need D <= 256 (the Z contraction's output width); use the FP32 form");
-    b->fused = c->akind != FBSDE_NAIS && L <= kFusedMaxDepth && b->Dp <= 256;
+    b->fused = L <= kFusedMaxDepth && b->Dp <= 256;
     b->f8 = c->prec == FBSDE_FP8_HIDDEN;
-    if (b->f8 && (!b->fused || w % 32 != 0))
+    if (b->f8 && (!b->fused || c->akind == FBSDE_NAIS || w % 32 != 0))
         return set_err(c, FBSDE_ERR_UNSUPPORTED,
                        "FP8 hidden layers need an FC or ResNet network with depth <= 8, D <= 256 and a width "
                        "that is a multiple of 32");
@@ -140,7 +140,7 @@ fbsde_status bf16_create(fbsde_ctx* c) {
     if (b->fused) {
         add((size_t)(L > 0 ? L : 1) * b->G_stride * sizeof(bf16));
         add((size_t)b->grid * (2 * L + 2) * 128 * w * sizeof(bf16));
-        add((size_t)(L + 3) * w * sizeof(float));
+        add((size_t)(2 * L + 3) * w * sizeof(float));
     }
     if (b->f8) {
         for (int l = 1; l <= L; ++l) add((size_t)w * b->wp8);
@@ -183,7 +183,7 @@ fbsde_status bf16_create(fbsde_ctx* c) {
     if (b->fused) {
         b->G = (bf16*)take((size_t)(L > 0 ? L : 1) * b->G_stride * sizeof(bf16));
         b->scratch = (bf16*)take((size_t)b->grid * (2 * L + 2) * 128 * w * sizeof(bf16));
-        b->pvec = (float*)take((size_t)(L + 3) * w * sizeof(float));
+        b->pvec = (float*)take((size_t)(2 * L + 3) * w * sizeof(float));
     }
     if (b->f8) {
         for (int l = 1; l <= L; ++l) b->W8[l] = (uint8_t*)take((size_t)w * b->wp8);
@@ -840,9 +840,9 @@ fbsde_status bf16_wgrad_tail(fbsde_ctx* c, const float* theta, float* grad) {
             add_pair(ax, b->tAB[l], b->tX, P);
             add_pair(ax, b->tE[l], b->tV, P);
             FBSDE_TRY(wgrad(c, ax, D, grad + pl.B[l], K0, 1));
-            FBSDE_TRY(nais_chain_R(c, theta, grad, l));
         }
     }
+    if (nais) FBSDE_TRY(nais_chain_R(c, theta, grad));  // dR = -R (dA + dA^T)
     {
         TcArgs ax = nt_args(c, w, b->Dn);
         add_pair(ax, b->tAB[0], b->tX, P);

@@ -141,6 +141,17 @@ def test_multi_tile_width256(P, prec):
 
 
 @pytest.mark.parametrize("prec", ["fp32", "bf16"])
+def test_multi_tile_nais_width256(P, prec):
+    # the NAIS-Net workload's shape (HJB, D = 100, NAIS-Net 6 x 256) over
+    # several 128-point tiles (P = 9 * 65 = 585); D = 100 leaves the second
+    # 64-wide input slice ragged
+    prob = P.ProblemSpec(kind="hjb", D=100, N=64, M=9, x0=[0.0] * 100)
+    arch = P.ArchSpec(kind="nais", width=256, depth=6, act="tanh", prec=prec)
+    # perturbed so that u(0, 0) is not zero (at the initial Theta it is exactly 0)
+    _check_eval(P, prob, arch, perturb=0.05)
+
+
+@pytest.mark.parametrize("prec", ["fp32", "bf16"])
 @pytest.mark.parametrize("case", ["D1_N1_M1", "depth0", "M1"])
 def test_edge_cases(P, case, prec):
     if case == "D1_N1_M1":
@@ -461,14 +472,16 @@ def test_full_size_workload_sampled_against_the_oracle(P):
     sf.close()
 
 
+@pytest.mark.parametrize("kind", ["resnet", "nais"])
 @pytest.mark.parametrize("case", ["D200", "D256", "depth8", "depth9_layered"])
-def test_fused_limits(P, case):
+def test_fused_limits(P, case, kind):
     # the fused kernels' limits (D <= 256, depth <= 8) and just past the
-    # depth limit, where the layered tcgen05 path takes over
+    # depth limit, where the layered tcgen05 path takes over; NAIS-Net streams
+    # up to four 64-wide input slices per block beside its weights
     D, L = {"D200": (200, 2), "D256": (256, 1), "depth8": (5, 8), "depth9_layered": (5, 9)}[case]
     x0 = [1.0 if i % 2 == 0 else 0.5 for i in range(D)]
     prob = P.ProblemSpec(kind="bsb", D=D, N=3, M=16, x0=x0)
-    arch = P.ArchSpec(kind="resnet", width=32, depth=L, act="tanh", prec="bf16")
+    arch = P.ArchSpec(kind=kind, width=32, depth=L, act="tanh", prec="bf16", h=0.5 if kind == "nais" else 1.0)
     _check_eval(P, prob, arch, seed=21, it=2, perturb=0.05)
 
 
