@@ -106,7 +106,8 @@ typedef struct {
 /* Architecture specification (Section 3.1). */
 typedef struct {
     int kind;          /* fbsde_arch_kind                                       */
-    int width;         /* w, multiple of 16, 16 <= w <= 256                      */
+    int width;         /* w, multiple of 16, 16 <= w <= 512 (the fused kernels  */
+                       /* serve w <= 256; wider layers run layered)          */
     int depth;         /* L hidden layers / blocks, 0 <= L <= 16                */
     int act;           /* fbsde_act                                             */
     double h;          /* NAIS step h > 0 (Section 3.1); ignored otherwise      */

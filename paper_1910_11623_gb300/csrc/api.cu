@@ -78,7 +78,7 @@ static std::string validate(const fbsde_problem* pb, const fbsde_arch* ar, int N
     if (ar->kind != FBSDE_FC && ar->kind != FBSDE_RESNET && ar->kind != FBSDE_NAIS)
         return "arch.kind must be FBSDE_FC, FBSDE_RESNET or FBSDE_NAIS";
     if (ar->width < 16 || ar->width > kMaxWidth || ar->width % 16 != 0)
-        return "arch.width must be a multiple of 16 in [16, 256]";
+        return "arch.width must be a multiple of 16 in [16, 512]";
     if (ar->depth < 0 || ar->depth > kMaxDepth) return "arch.depth must be in [0, 16]";
     if (ar->act != FBSDE_SIN && ar->act != FBSDE_TANH) return "arch.act must be FBSDE_SIN or FBSDE_TANH";
     if (ar->kind == FBSDE_NAIS) {

@@ -13,7 +13,7 @@
 namespace fbsde {
 
 constexpr int kMaxDepth = 16;
-constexpr int kMaxWidth = 256;
+constexpr int kMaxWidth = 512;
 
 // Offsets of each tensor inside the flat FP32 parameter vector (the order is
 // documented in fbsde.h).  For NAIS, W[l] is R_l, b[l] is C_l, B[l] is B_l.

@@ -8,7 +8,9 @@
 //            B [K x N] both MN-major: the weight gradients, where k runs over
 //            points; blockIdx.y splits K into chunks of args.kchunk.
 //
-// One CTA computes a 128 x N tile (N <= 256).  Warp 0 streams 64-wide K
+// One CTA computes a 128 x Nt tile: Nt = N for N <= 256, else blockIdx.z
+// picks 256 of the N columns (weight maps of such widths have boxes of 256
+// rows; the last box may run past the matrix and reads zeros).  Warp 0 streams 64-wide K
 // slices of A and B into a 4-stage shared-memory ring with TMA (128-byte
 // swizzle); warp 1 allocates TMEM and one of its threads issues the
 // tcgen05.mma instructions (K = 16 each) and commits stage releases and the
@@ -34,7 +36,7 @@ constexpr int kTcMaxPairs = 2;
 
 struct TcPair {
     CUtensorMap a;  // NT: [rows x K], box {64, 128}; TN: [K x rows], box {64, 64}
-    CUtensorMap b;  // NT: [N x K],    box {64, N};   TN: [K x N],    box {64, 64}
+    CUtensorMap b;  // NT: [N x K],    box {64, min(N, 256)};   TN: [K x N],    box {64, 64}
     int K;
 };
 
@@ -42,7 +44,7 @@ struct TcArgs {
     TcPair pr[kTcMaxPairs];
     int npairs;
     int rows;    // output rows (NT: points; TN: output features)
-    int N;       // output columns: multiple of 16, 16..256
+    int N;       // output columns: multiple of 16, 16..512 (tiles of 256 over blockIdx.z)
     int kchunk;  // TN: K range per blockIdx.y, multiple of 64
     int* err;    // device flag set when a bounded wait gives up
     // TN, optional (NULL: off): cs_part[blockIdx.y * rows + m] = sum over the
@@ -62,8 +64,10 @@ template <bool TN, class Epi>
 __global__ void __launch_bounds__(192, 1) tc_gemm_kernel(const __grid_constant__ TcArgs args, const Epi epi) {
     extern __shared__ uint8_t smem_raw[];
     uint8_t* smem = (uint8_t*)(((uintptr_t)smem_raw + 1023) & ~(uintptr_t)1023);
-    const int N = args.N;
-    const uint32_t stage_bytes = tc_stage_bytes(N);
+    const int n0 = (int)blockIdx.z * 256;          // first column of this CTA
+    const int N = min(256, args.N - n0);           // its columns
+    const int Nbox = min(256, args.N);             // NT: weight rows per stage
+    const uint32_t stage_bytes = tc_stage_bytes(Nbox);
     uint64_t* full = (uint64_t*)(smem + kTcStages * stage_bytes);
     uint64_t* empty = full + kTcStages;
     uint64_t* accf = empty + kTcStages;
@@ -77,7 +81,7 @@ __global__ void __launch_bounds__(192, 1) tc_gemm_kernel(const __grid_constant__
 
     // stage release: the MMA's commit, plus one arrival per epilogue warp
     // when they read the stages for the column sums
-    const bool colsums = TN && args.cs_part != nullptr;
+    const bool colsums = TN && args.cs_part != nullptr && blockIdx.z == 0;
     if (threadIdx.x == 0) {
         for (int s = 0; s < kTcStages; ++s) {
             tc::mbar_init(&full[s], 1);
@@ -117,15 +121,15 @@ __global__ void __launch_bounds__(192, 1) tc_gemm_kernel(const __grid_constant__
                     uint8_t* sa = smem + (size_t)s * stage_bytes;
                     uint8_t* sb = sa + 16384;
                     if (!TN) {
-                        tc::mbar_expect_tx(&full[s], 16384u + (uint32_t)N * 128u);
+                        tc::mbar_expect_tx(&full[s], 16384u + (uint32_t)Nbox * 128u);
                         tc::tma_load_2d(sa, &pr.a, &full[s], k0, m0);
-                        tc::tma_load_2d(sb, &pr.b, &full[s], k0, 0);
+                        tc::tma_load_2d(sb, &pr.b, &full[s], k0, n0);
                     } else {
                         const int na = (args.rows - m0 > 64) ? 2 : 1;
                         const int nb = (N + 63) / 64;
                         tc::mbar_expect_tx(&full[s], (uint32_t)(na + nb) * 8192u);
                         for (int j = 0; j < na; ++j) tc::tma_load_2d(sa + j * 8192, &pr.a, &full[s], m0 + 64 * j, k0);
-                        for (int j = 0; j < nb; ++j) tc::tma_load_2d(sb + j * 8192, &pr.b, &full[s], 64 * j, k0);
+                        for (int j = 0; j < nb; ++j) tc::tma_load_2d(sb + j * 8192, &pr.b, &full[s], n0 + 64 * j, k0);
                     }
                 }
             }
@@ -227,7 +231,7 @@ __global__ void __launch_bounds__(192, 1) tc_gemm_kernel(const __grid_constant__
                 float v[16];
 #pragma unroll
                 for (int j = 0; j < 16; ++j) v[j] = __uint_as_float(r[j]);
-                if (row < args.rows) epi(row, c0, v, (int)blockIdx.y);
+                if (row < args.rows) epi(row, n0 + c0, v, (int)blockIdx.y);
             }
         } else if (lane == 0) {
             if (args.err) atomicExch(args.err, 1);
@@ -253,8 +257,8 @@ inline cudaError_t tc_gemm(const TcArgs& a, int splits, const Epi& e, cudaStream
         if (err != cudaSuccess) return err;
         configured = true;
     }
-    dim3 grid((a.rows + 127) / 128, TN ? splits : 1);
-    tc_gemm_kernel<TN, Epi><<<grid, 192, tc_smem_bytes(a.N), st>>>(a, e);
+    dim3 grid((a.rows + 127) / 128, TN ? splits : 1, (a.N + 255) / 256);
+    tc_gemm_kernel<TN, Epi><<<grid, 192, tc_smem_bytes(a.N < 256 ? a.N : 256), st>>>(a, e);
     return cudaGetLastError();
 }
 

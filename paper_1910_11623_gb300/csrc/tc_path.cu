@@ -102,11 +102,12 @@ fbsde_status bf16_create(fbsde_ctx* c) {
     const size_t Pm = c->Pmax();
     b->OP_stride = rup(Pm * b->wp, 128);
     const size_t nl = (size_t)L + 1;
-    // per-tile fused kernels: FC / ResNet / NAIS-Net, depth <= kFusedMaxDepth, D <= 256
+    // per-tile fused kernels: FC / ResNet / NAIS-Net, depth <= kFusedMaxDepth,
+    // D <= 256, width <= 256 (the accumulator and the residual share TMEM)
     if (b->Dn > 256)
         return set_err(c, FBSDE_ERR_UNSUPPORTED,
                        "the BF16 forms need D <= 256 (the Z contraction's output width); use the FP32 form");
-    b->fused = L <= kFusedMaxDepth && b->Dp <= 256;
+    b->fused = L <= kFusedMaxDepth && b->Dp <= 256 && w <= 256;
     b->f8 = c->prec == FBSDE_FP8_HIDDEN;
     if (b->f8 && (!b->fused || c->akind == FBSDE_NAIS || w % 32 != 0))
         return set_err(c, FBSDE_ERR_UNSUPPORTED,
@@ -206,12 +207,14 @@ fbsde_status bf16_create(fbsde_ctx* c) {
         ok &= map2d(&b->tHD[l], b->HDb[l], b->wp, P64, b->wp, 64);
         ok &= map2d(&b->tAB[l], b->ABb[l], b->wp, P64, b->wp, 64);
     }
-    ok &= map2d(&b->mWinx, b->Winx, b->Dp, w, b->Dp, w);
+    // weight maps: boxes of up to 256 rows (wider layers run in column tiles)
+    const uint32_t wbox = (uint32_t)(w < 256 ? w : 256);
+    ok &= map2d(&b->mWinx, b->Winx, b->Dp, w, b->Dp, wbox);
     ok &= map2d(&b->mWinxT, b->WinxT, b->wp, b->Dn, b->wp, b->Dn);
     for (int l = 1; l <= L; ++l) {
-        ok &= map2d(&b->mW[l], b->W[l], b->wp, w, b->wp, w);
-        ok &= map2d(&b->mWT[l], b->WT[l], b->wp, w, b->wp, w);
-        ok &= map2d(&b->mBx[l], b->Bx[l], b->Dp, w, b->Dp, w);
+        ok &= map2d(&b->mW[l], b->W[l], b->wp, w, b->wp, wbox);
+        ok &= map2d(&b->mWT[l], b->WT[l], b->wp, w, b->wp, wbox);
+        ok &= map2d(&b->mBx[l], b->Bx[l], b->Dp, w, b->Dp, wbox);
         ok &= map2d(&b->mBxT[l], b->BxT[l], b->wp, b->Dn, b->wp, b->Dn);
         if (b->f8) ok &= map2d_u8(&b->mW8[l], b->W8[l], b->wp8, w, b->wp8, w);
     }

@@ -66,7 +66,7 @@ def _specs(**kw):
     (dict(T=-1.0), "problem.T"),
     (dict(sigma=-0.1), "sigma"),
     (dict(a_width=20), "arch.width"),
-    (dict(a_width=512), "arch.width"),
+    (dict(a_width=528), "arch.width"),
     (dict(a_depth=17), "arch.depth"),
     (dict(a_kind="nais", a_eps=0.0), "arch.eps"),
     (dict(a_kind="nais", a_h=0.0), "arch.h"),

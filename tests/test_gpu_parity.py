@@ -141,6 +141,16 @@ def test_multi_tile_width256(P, prec):
 
 
 @pytest.mark.parametrize("prec", ["fp32", "bf16"])
+@pytest.mark.parametrize("kind,width", [("resnet", 512), ("nais", 512), ("fc", 384)])
+def test_wide_networks(P, prec, kind, width):
+    # widths past the fused kernels' 256: the layered path in column tiles of
+    # 256 (384 leaves a half-filled last tile); P = 40 * 4 = 160 points
+    prob = P.ProblemSpec(kind="bsb", D=10, N=3, M=40, x0=[1.0, 0.5] * 5)
+    arch = P.ArchSpec(kind=kind, width=width, depth=2, act="tanh", prec=prec, h=0.5 if kind == "nais" else 1.0)
+    _check_eval(P, prob, arch, seed=8, it=2, perturb=0.02)
+
+
+@pytest.mark.parametrize("prec", ["fp32", "bf16"])
 def test_multi_tile_nais_width256(P, prec):
     # the NAIS-Net workload's shape (HJB, D = 100, NAIS-Net 6 x 256) over
     # several 128-point tiles (P = 9 * 65 = 585); D = 100 leaves the second
