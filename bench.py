@@ -55,6 +55,11 @@ def parse_args():
                     help="Adam steps of the FP8-hidden-layer form (timed for speed, then trained; 0: skip)")
     ap.add_argument("--nais-steps", type=int, default=5,
                     help="timed steps of the HJB NAIS-Net workload in both forms (0: skip)")
+    ap.add_argument("--wide-steps", type=int, default=3,
+                    help="train steps timed per form on the NAIS-Net 6 x 512 network (BSB, M = 16384); 0 skips")
+    ap.add_argument("--wide-accuracy-steps", type=int, default=0,
+                    help="> 0: also train that network single-level and multilevel to |Y0 err| <= 1%% "
+                         "(at most this many steps on the N = 64 grid)")
     ap.add_argument("--batched-steps", type=int, default=3,
                     help="timed group steps of the 32 uneven instances (0: skip)")
     ap.add_argument("--M", type=int, default=0,
@@ -312,6 +317,31 @@ def multilevel_run(P, w, target, max_steps):
     res = {"levels": levels, "coarse_steps_per_level": P.workloads.MULTILEVEL_COARSE_STEPS,
            "per_level": per_level, "time_to_1pct_s": hit[0] if hit else None,
            "steps_to_1pct": hit[1] if hit else None, "wall_s": time.perf_counter() - t0}
+    s.close()
+    return res
+
+
+def single_level_run(P, w, target, max_steps):
+    """Training on the target grid alone from Theta_0 until |Y0 - closed form|
+    <= 1% (checked every 50 steps), in schedule calls of 50 steps."""
+    import torch
+    N = w.problem.N
+    s = P.Solver(w.problem, w.arch, seed=w.seed)
+    th = s.init_params()
+    m, v = torch.zeros_like(th), torch.zeros_like(th)
+    torch.cuda.synchronize()
+    t0 = time.perf_counter()
+    step, hit, err = 1, None, None
+    while step <= max_steps:
+        k = min(50, max_steps - step + 1)
+        _, y0 = s.train_schedule(th, m, v, [N], [k], step, w.lr)
+        step += k
+        err = abs(y0[-1].item() - target) / target
+        if err <= 0.01:
+            hit = (time.perf_counter() - t0, step - 1)
+            break
+    res = {"N": N, "time_to_1pct_s": hit[0] if hit else None, "steps_to_1pct": hit[1] if hit else None,
+           "y0_rel_err": err, "wall_s": time.perf_counter() - t0}
     s.close()
     return res
 
@@ -608,6 +638,34 @@ def main():
             out["nais_hjb"] = res_n
         except Exception as exc:
             out["nais_hjb"] = {"error": f"{type(exc).__name__}: {exc}"}
+
+    # the wide NAIS-Net of the multilevel study (BSB, D = 100, M = 16384,
+    # NAIS-Net 6 x 512): width 512 runs on the layered tensor-core path
+    if out is not None and args.wide_steps > 0:
+        try:
+            ww = P.workloads.WORKLOADS["bsb_d100_n64_m16384_nais6x512_tanh"]
+            res_w = {"workload": ww.name}
+            for prec, n in (("bf16", args.wide_steps), ("fp32", 1)):
+                wp_ = ww.with_prec(prec)
+                sw = P.Solver(wp_.problem, wp_.arch, seed=ww.seed, stream=torch.cuda.Stream())
+                thw = sw.init_params()
+                mw, vw = torch.zeros_like(thw), torch.zeros_like(thw)
+                with torch.cuda.stream(sw.stream):
+                    sw.train_step(thw, mw, vw, 1, ww.lr)
+                msw = time_steps(sw, thw, mw, vw, 2, n, ww.lr)
+                res_w[prec] = {"value": n / (msw / 1000.0), "unit": "it/s", "steps": n}
+                sw.close()
+                del thw, mw, vw
+                torch.cuda.empty_cache()
+            res_w["speedup_bf16_vs_fp32"] = res_w["bf16"]["value"] / res_w["fp32"]["value"]
+            if args.wide_accuracy_steps > 0:
+                wb = ww.with_prec("bf16")
+                target = P.workloads.bsb_y0(wb.problem.x0)
+                res_w["single_level"] = single_level_run(P, wb, target, args.wide_accuracy_steps)
+                res_w["multilevel"] = multilevel_run(P, wb, target, args.wide_accuracy_steps)
+            out["wide_nais"] = res_w
+        except Exception as exc:
+            out["wide_nais"] = {"error": f"{type(exc).__name__}: {exc}"}
 
     if out is not None and args.batched_steps > 0 and world == 1:
         try:

@@ -48,6 +48,12 @@ WORKLOADS = {
         "hjb_d100_n64_m8192_nais6x256_tanh",
         ProblemSpec(kind="hjb", D=100, N=64, M=8192, x0=[0.0] * 100),
         ArchSpec(kind="nais", width=256, depth=6, act="tanh"), seed=0, adam_steps=5000),
+    # 100-D BSB, N = 64, M = 16384, NAIS 6 blocks x 512 tanh: the wide network
+    # of the multilevel study (Section 3.2); width 512 runs on the layered path
+    "bsb_d100_n64_m16384_nais6x512_tanh": Workload(
+        "bsb_d100_n64_m16384_nais6x512_tanh",
+        ProblemSpec(kind="bsb", D=100, N=64, M=16384, x0=bsb_x0(100)),
+        ArchSpec(kind="nais", width=512, depth=6, act="tanh"), seed=0, adam_steps=5000),
 }
 
 # Closed-form anchors (Section 4): BSB u(0, x0) and HJB u(0, 0) (Cole-Hopf,
@@ -74,7 +80,7 @@ MULTILEVEL_COARSE_STEPS = 100
 def batched_instances(seed: int = 0, n: int = 32, budget_gb: float = 140.0):
     """Uneven independent instances (half BSB, half HJB): D from
     {10, 20, 50, 100, 200}, N from {16, 32, 64, 128}, M from {1024, 4096,
-    16384}, ResNet 4 x w tanh with w from {128, 256}, all seeded.  The
+    16384}, ResNet 4 x w tanh with w from {128, 256, 512}, all seeded.  The
     largest instances' M is halved until the estimated device memory of all
     workspaces fits `budget_gb`.  Returns a list of Workloads."""
     import random
@@ -85,14 +91,16 @@ def batched_instances(seed: int = 0, n: int = 32, budget_gb: float = 140.0):
         D = rng.choice([10, 20, 50, 100, 200])
         N = rng.choice([16, 32, 64, 128])
         M = rng.choice([1024, 4096, 16384])
-        w = rng.choice([128, 256])
+        w = rng.choice([128, 256, 512])
         specs.append([kind, D, N, M, w])
 
     def est_bytes(D, N, M, w, L=4):
         P = M * (N + 1)
         Dp = (D + 63) // 64 * 64
-        per_point = 4 * (L + 1) * 2 * w + L * 2 * w + 2 * 2 * Dp + 4 * 4 * D + 64
-        return P * per_point + 152 * (2 * L + 2) * 128 * w * 2
+        per_point = 4 * (L + 1) * 2 * w + 2 * 2 * Dp + 4 * 4 * D + 64
+        if w <= 256:  # fused kernels: g_l and per-CTA scratch
+            return P * (per_point + L * 2 * w) + 152 * (2 * L + 2) * 128 * w * 2
+        return P * (per_point + 6 * (L + 1) * 4 * w)  # layered: FP32 per-layer tensors
 
     while sum(est_bytes(D, N, M, w) for _, D, N, M, w in specs) > budget_gb * 1e9:
         big = max(range(n), key=lambda i: est_bytes(*specs[i][1:]))
