@@ -232,9 +232,7 @@ def sample_paths(problem: Problem, seed: int, iteration: int, paths=None):
     paths: optional array of path indices (a subset of 0..M-1); the noise of a
     path depends only on (seed, iteration, path, step, dimension)."""
     dW = philox.brownian_increments(seed, iteration, problem.M, problem.N,
-                                    problem.D, problem.T)
-    if paths is not None:
-        dW = dW[:, np.asarray(paths)]
+                                    problem.D, problem.T, paths)
     return dW, forward_sde(problem, dW)
 
 

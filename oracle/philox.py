@@ -97,14 +97,16 @@ def box_muller(words):
                      r23 * np.cos(ang23), r23 * np.sin(ang23)], axis=-1)
 
 
-def brownian_counters(iteration: int, M: int, N: int, D: int):
+def brownian_counters(iteration: int, M: int, N: int, D: int, paths=None):
     """Philox counters for the increments of one iteration.
 
     Counter of (step n, path m, dimension quad q) is (q, n, m, iteration);
-    quad q covers dimensions 4q .. 4q+3.  Returns uint64 [N, M, Q, 4].
+    quad q covers dimensions 4q .. 4q+3.  Returns uint64 [N, M, Q, 4], or
+    [N, len(paths), Q, 4] for the paths listed in `paths`.
     """
     Q = (D + 3) // 4
-    n, m, q = np.meshgrid(np.arange(N), np.arange(M), np.arange(Q), indexing="ij")
+    ms = np.arange(M) if paths is None else np.asarray(paths)
+    n, m, q = np.meshgrid(np.arange(N), ms, np.arange(Q), indexing="ij")
     it = np.full_like(n, int(iteration) & 0xFFFFFFFF)
     return np.stack([q, n, m, it], axis=-1).astype(np.uint64)
 
@@ -116,12 +118,14 @@ def brownian_words(seed: int, iteration: int, M: int, N: int, D: int):
     return w.reshape(N, M, -1)
 
 
-def brownian_increments(seed: int, iteration: int, M: int, N: int, D: int, T: float):
+def brownian_increments(seed: int, iteration: int, M: int, N: int, D: int, T: float, paths=None):
     """Delta W_n^m ~ N(0, Delta t) with Delta t = T/N (Section 2.2, Eq. disc
-    equations, first line).  Returns FP64 [N, M, D]."""
-    ctr = brownian_counters(iteration, M, N, D)
+    equations, first line).  Returns FP64 [N, M, D] (with `paths`: only the
+    listed paths, [N, len(paths), D]; a path's noise depends on its own
+    counters alone)."""
+    ctr = brownian_counters(iteration, M, N, D, paths)
     z = box_muller(philox4x32_10(ctr, noise_key(seed)))
-    z = z.reshape(N, M, -1)[:, :, :D]
+    z = z.reshape(N, ctr.shape[1], -1)[:, :, :D]
     return np.sqrt(T / N) * z
 
 

@@ -451,14 +451,17 @@ def test_fp8_rejects_unsupported_shapes(P):
         P.Solver(prob, P.ArchSpec(kind="nais", width=32, depth=2, act="tanh", prec="fp8"))
 
 
-def test_full_size_workload_sampled_against_the_oracle(P):
-    # the measured workload at full size (M = 4096, N = 64, D = 100, ResNet
-    # 5 x 256 tanh) through the same kernels and launch configuration the
-    # bench times: Y, Z and the per-path loss of 16 sampled paths against the
-    # oracle (a path's values depend on that path alone); the loss and the
+@pytest.mark.parametrize("name", ["bsb_d100_n64_m4096_resnet5x256_tanh", "hjb_d100_n64_m8192_nais6x256_tanh",
+                                  "bsb_d100_n64_m16384_nais6x512_tanh"])
+def test_full_size_workload_sampled_against_the_oracle(P, name):
+    # the bench's workloads at full size (the measured ResNet 5 x 256 one, the
+    # HJB NAIS-Net 6 x 256 one on the fused kernels, the NAIS-Net 6 x 512 one
+    # on the layered path) through the same kernels and launch configuration
+    # the bench times: Y, Z and the per-path loss of 16 sampled paths against
+    # the oracle (a path's values depend on that path alone); the loss and the
     # gradient (sums over all paths) against the FP32 form at the same size,
     # itself pinned to the oracle at 1e-5 at small sizes
-    w = P.workloads.WORKLOADS["bsb_d100_n64_m4096_resnet5x256_tanh"]
+    w = P.workloads.WORKLOADS[name]
     wb, wf = w.with_prec("bf16"), w.with_prec("fp32")
     sb = _solver(P, wb.problem, wb.arch, seed=w.seed)
     th64, th = _theta_pair(P, sb, wb.problem, wb.arch, w.seed)
