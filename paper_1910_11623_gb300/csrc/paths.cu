@@ -155,6 +155,7 @@ __device__ __forceinline__ float warp_sum(float v) {
 //   alpha = 2 r_{n-1} [n >= 1] - 2 r_n (1 + phi_y dt) [n < N] + 2 r_T [n = N]
 //   v     = -2 r_n (phi_z dt + sigma(X_n) dW_n) [n < N] + 2 (Z_N - grad g) [n = N, term on]
 // and the per-path loss sum_n r_n^2 + r_T^2 (+ |Z_N - grad g|^2), accumulated in FP64.
+// Serves fbsde_residual_loss_noalloc, whose caller passes the increments.
 __global__ void k_seeds(ProblemDev pd, const float* __restrict__ X, const float* __restrict__ dW,
                         const float* __restrict__ Y, const float* __restrict__ Z,
                         float* __restrict__ alpha, float* __restrict__ V,
@@ -260,10 +261,12 @@ fbsde_status copy_path_loss(fbsde_ctx* ctx, float* out) {
     return FBSDE_OK;
 }
 
-// The same residuals and seeds as k_seeds, parallel over the points: one warp
-// per point (n, m), n < N, forms r_n (Eq. "loss") and v_n, and stores r_n;
+// One warp per point (n, m), n < N, forms the residual of Eq. "loss"
+//   r_n = Y_{n+1} - Y_n - phi(X_n, Y_n, Z_n) dt - Z_n^T sigma(X_n) dW_n
+// and the seed v_n = -2 r_n (phi_z dt + sigma(X_n) dW_n), and stores r_n;
 // k_seeds_paths then forms alpha_n from r_{n-1} and r_n, the per-path loss
-// (FP64, fixed order) and the terminal point.
+// (FP64, fixed order) and the terminal point.  Lane = dimension quad (16-byte
+// loads when D is a multiple of 4).
 __global__ void k_resid(ProblemDev pd, const float* __restrict__ X, const float* __restrict__ dW,
                         const float* __restrict__ Y, const float* __restrict__ Z, float* __restrict__ rbuf,
                         float* __restrict__ V, __nv_bfloat16* __restrict__ Vb, int ldb) {
@@ -271,31 +274,79 @@ __global__ void k_resid(ProblemDev pd, const float* __restrict__ X, const float*
     const long wp = ((long)blockIdx.x * blockDim.x + threadIdx.x) >> 5;
     if (wp >= (long)pd.N * pd.M) return;
     const size_t p = (size_t)wp;  // n * M + m
-    const int D = pd.D;
+    const int D = pd.D, Q = (D + 3) >> 2;
     const bool bsb = pd.kind == FBSDE_BSB;
+    const bool vec = (D & 3) == 0;
     const float sqrt2 = 1.41421356237309515f;
     const float* x = X + p * D;
     const float* z = Z + p * D;
-    const float* dw = dW + p * D;
+    const float* w = dW + p * D;
+    // quad q of this point: x, z and dW of dimensions 4q .. 4q+3 (zero past D)
+    auto quad = [&](int q, float (&xv)[4], float (&zv)[4], float (&dw)[4]) {
+        const int d0 = 4 * q;
+        if (vec) {
+            const float4 a = reinterpret_cast<const float4*>(x)[q];
+            const float4 b = reinterpret_cast<const float4*>(z)[q];
+            const float4 c = reinterpret_cast<const float4*>(w)[q];
+            xv[0] = a.x; xv[1] = a.y; xv[2] = a.z; xv[3] = a.w;
+            zv[0] = b.x; zv[1] = b.y; zv[2] = b.z; zv[3] = b.w;
+            dw[0] = c.x; dw[1] = c.y; dw[2] = c.z; dw[3] = c.w;
+        } else {
+#pragma unroll
+            for (int j = 0; j < 4; ++j) {
+                xv[j] = d0 + j < D ? x[d0 + j] : 0.f;
+                zv[j] = d0 + j < D ? z[d0 + j] : 0.f;
+                dw[j] = d0 + j < D ? w[d0 + j] : 0.f;
+            }
+        }
+    };
     float zx = 0.f, zsdw = 0.f, zz = 0.f;
-    for (int d = lane; d < D; d += 32) {
-        const float xd = x[d], zd = z[d];
-        const float sdw = bsb ? pd.sigma * xd * dw[d] : sqrt2 * dw[d];
-        zx = fmaf(zd, xd, zx);
-        zsdw = fmaf(zd, sdw, zsdw);
-        zz = fmaf(zd, zd, zz);
+    for (int q = lane; q < Q; q += 32) {
+        float xv[4], zv[4], dw[4];
+        quad(q, xv, zv, dw);
+#pragma unroll
+        for (int j = 0; j < 4; ++j) {  // padded dimensions carry x = z = 0
+            const float sdw = bsb ? pd.sigma * xv[j] * dw[j] : sqrt2 * dw[j];
+            zx = fmaf(zv[j], xv[j], zx);
+            zsdw = fmaf(zv[j], sdw, zsdw);
+            zz = fmaf(zv[j], zv[j], zz);
+        }
     }
     zx = warp_sum(zx); zsdw = warp_sum(zsdw); zz = warp_sum(zz);
     const float yn = Y[p], yn1 = Y[p + pd.M];
     const float phi = bsb ? pd.r * (yn - zx) : zz;
     const float r = yn1 - yn - phi * pd.dt - zsdw;
     if (lane == 0) rbuf[p] = r;
-    for (int d = lane; d < D; d += 32) {
-        const float sdw = bsb ? pd.sigma * x[d] * dw[d] : sqrt2 * dw[d];
-        const float phiz = bsb ? -pd.r * x[d] : 2.f * z[d];
-        const float v = -2.f * r * (phiz * pd.dt + sdw);
-        if (V) V[p * D + d] = v;
-        if (Vb) Vb[p * ldb + d] = __float2bfloat16_rn(v);
+    for (int q = lane; q < Q; q += 32) {
+        float xv[4], zv[4], dw[4], v[4];
+        quad(q, xv, zv, dw);
+#pragma unroll
+        for (int j = 0; j < 4; ++j) {
+            const float sdw = bsb ? pd.sigma * xv[j] * dw[j] : sqrt2 * dw[j];
+            const float phiz = bsb ? -pd.r * xv[j] : 2.f * zv[j];
+            v[j] = -2.f * r * (phiz * pd.dt + sdw);
+        }
+        const int d0 = 4 * q;
+        if (vec) {
+            if (V) reinterpret_cast<float4*>(V + p * D)[q] = make_float4(v[0], v[1], v[2], v[3]);
+            if (Vb && (ldb & 3) == 0) {
+                __nv_bfloat162 lo = __floats2bfloat162_rn(v[0], v[1]), hi = __floats2bfloat162_rn(v[2], v[3]);
+                uint2 u;
+                u.x = *reinterpret_cast<uint32_t*>(&lo);
+                u.y = *reinterpret_cast<uint32_t*>(&hi);
+                *reinterpret_cast<uint2*>(Vb + p * ldb + d0) = u;
+            } else if (Vb) {
+#pragma unroll
+                for (int j = 0; j < 4; ++j) Vb[p * ldb + d0 + j] = __float2bfloat16_rn(v[j]);
+            }
+        } else {
+#pragma unroll
+            for (int j = 0; j < 4; ++j)
+                if (d0 + j < D) {
+                    if (V) V[p * D + d0 + j] = v[j];
+                    if (Vb) Vb[p * ldb + d0 + j] = __float2bfloat16_rn(v[j]);
+                }
+        }
     }
 }
 
