@@ -160,10 +160,10 @@ fbsde_status fbsde_create(const fbsde_problem* problem, const fbsde_arch* arch, 
     add((size_t)c->N_max * c->M * D);        // dW
     add(Pm); add(Pm * D); add(Pm); add(Pm * D); add(2 * Pm);  // Y Z alpha V ones_t
     add(Pm);                   // residuals r_n
-    add(2 * (size_t)c->M);     // path_loss (double)
+    add(4 * (size_t)c->M);     // per-path loss and alpha sums (double)
     if (c->akind == FBSDE_NAIS) { add(2 * L * w * w); }
     add(c->part_floats);
-    add(32); add(kMaxDepth + 1); add(16); // dscal, fscal, nonfinite
+    add(16); add(kMaxDepth + 1); add(16); // alpha_sum, fscal, nonfinite
     add(c->pl.total);          // gradient buffer of train_step
     if (c->prec == FBSDE_FP32) add(fp32_workspace_floats(c));
     c->arena_bytes = total * sizeof(float);
@@ -184,11 +184,11 @@ fbsde_status fbsde_create(const fbsde_problem* problem, const fbsde_arch* arch, 
     c->Y = take(Pm); c->Z = take(Pm * D); c->alpha = take(Pm); c->V = take(Pm * D);
     c->ones_t = take(2 * Pm);
     c->rbuf = take(Pm);
-    c->path_loss_d = (double*)take(2 * (size_t)c->M);
+    c->path_loss_d = (double*)take(4 * (size_t)c->M);
     if (c->akind == FBSDE_NAIS)
         for (int l = 1; l <= c->L; ++l) { c->Amat[l] = take(w * w); c->gA[l] = take(w * w); }
     c->part = take(c->part_floats);
-    c->dscal = (double*)take(32);
+    c->alpha_sum = take(16);
     c->fscal = take(kMaxDepth + 1);
     c->nonfinite = (int*)take(16);
     c->gradbuf = take(c->pl.total);

@@ -517,10 +517,8 @@ fbsde_status fp32_backward(fbsde_ctx* c, const float* theta, float* grad) {
         g.pair[0] = {f.H[L], c->alpha, Pi, w, 1};
         g.pair[1] = {f.HD[L], c->ones_t, Pi, w, 2};
         FBSDE_TRY(tn_reduce(c, g, 0, 1, grad + pl.wo, 1, 0));
-        GemmArgs gb{};
-        gb.npairs = 1; gb.Mrows = 1; gb.Ncols = 1;
-        gb.pair[0] = {c->alpha, c->ones_t, Pi, 1, 2};
-        FBSDE_TRY(tn_reduce(c, gb, 0, 1, grad + pl.bo, 1, 0));
+        // db_o = sum_p alpha_p, formed with the loss (k_loss_reduce)
+        FBSDE_CK(c, cudaMemcpyAsync(grad + pl.bo, c->alpha_sum, sizeof(float), cudaMemcpyDeviceToDevice, st));
     }
     k_check_finite<<<nblk(pl.total, 256), 256, 0, st>>>(pl.total, grad, c->nonfinite);
     FBSDE_CK_LAUNCH(c);

@@ -92,14 +92,14 @@ struct fbsde_ctx {
     float* alpha = nullptr;    // d loss / d Y_n       [(N_max+1) M]
     float* V = nullptr;        // d loss / d Z_n       [(N_max+1) M, D]
     float* ones_t = nullptr;   // (1, t_n) per point   [(N_max+1) M, 2]
-    double* path_loss_d = nullptr;  // per-path loss   [M]
+    double* path_loss_d = nullptr;  // per-path loss [M], then per-path sum of alpha [M]
     float* rbuf = nullptr;     // Y-residuals r_n      [N_max M]
     bool need_V32 = true;      // FP32 v_n consumed (FP32 form, layered BF16 sweeps)
     float* Amat[fbsde::kMaxDepth + 1] = {};  // NAIS A_l = -R^T R - eps I [w, w]
     float* gA[fbsde::kMaxDepth + 1] = {};    // NAIS d loss / d A_l       [w, w]
     float* part = nullptr;     // split-K partial sums
     size_t part_floats = 0;
-    double* dscal = nullptr;   // device scalars (loss accumulators, norms)
+    float* alpha_sum = nullptr;  // sum of alpha over all points (the gradient in b_o)
     float* fscal = nullptr;    // device float scalars (projection scales)
     int* nonfinite = nullptr;  // set when a loss/gradient entry is NaN/Inf
     float* gradbuf = nullptr;  // gradient of fbsde_train_step [num_params]

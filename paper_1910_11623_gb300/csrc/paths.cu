@@ -230,22 +230,33 @@ __global__ void k_seeds(ProblemDev pd, const float* __restrict__ X, const float*
 // Fixed-order reduction of the per-path losses (one block, so the result is
 // bit-reproducible), plus Y_0 = u(0, x0) (all paths start at x0, so it is the
 // network value at point 0) and the non-finite flag.
+// With path_alpha, the same fixed-order sum of the per-path alpha sums goes
+// to *alpha_sum (the gradient in the read-out bias b_o).
 __global__ void k_loss_reduce(const double* __restrict__ path_loss, int M,
                               const float* __restrict__ Y, float* __restrict__ loss_out,
-                              float* __restrict__ y0_out, int* __restrict__ nonfinite) {
-    __shared__ double sh[1024];
-    double acc = 0.0;
-    for (int m = threadIdx.x; m < M; m += blockDim.x) acc += path_loss[m];
+                              float* __restrict__ y0_out, int* __restrict__ nonfinite,
+                              const double* __restrict__ path_alpha, float* __restrict__ alpha_sum) {
+    __shared__ double sh[1024], sa[1024];
+    double acc = 0.0, acca = 0.0;
+    for (int m = threadIdx.x; m < M; m += blockDim.x) {
+        acc += path_loss[m];
+        if (path_alpha) acca += path_alpha[m];
+    }
     sh[threadIdx.x] = acc;
+    sa[threadIdx.x] = acca;
     __syncthreads();
     for (int s = blockDim.x / 2; s > 0; s >>= 1) {
-        if (threadIdx.x < s) sh[threadIdx.x] += sh[threadIdx.x + s];
+        if (threadIdx.x < s) {
+            sh[threadIdx.x] += sh[threadIdx.x + s];
+            sa[threadIdx.x] += sa[threadIdx.x + s];
+        }
         __syncthreads();
     }
     if (threadIdx.x == 0) {
         const double L = sh[0];
         if (loss_out) *loss_out = (float)L;
         if (y0_out) *y0_out = Y[0];
+        if (path_alpha) *alpha_sum = (float)sa[0];
         if (!isfinite(L) || !isfinite(Y[0])) *nonfinite = 1;
     }
 }
@@ -353,22 +364,27 @@ __global__ void k_resid(ProblemDev pd, const float* __restrict__ X, const float*
 __global__ void k_seeds_paths(ProblemDev pd, const float* __restrict__ X, const float* __restrict__ Y,
                               const float* __restrict__ Z, const float* __restrict__ rbuf,
                               float* __restrict__ alpha, float* __restrict__ V, double* __restrict__ path_loss,
-                              __nv_bfloat16* __restrict__ Vb, int ldb) {
+                              double* __restrict__ path_alpha, __nv_bfloat16* __restrict__ Vb, int ldb) {
     const int lane = threadIdx.x & 31;
     const int m = (int)(((long)blockIdx.x * blockDim.x + threadIdx.x) >> 5);
     if (m >= pd.M) return;
     const int D = pd.D;
     const bool bsb = pd.kind == FBSDE_BSB;
     const float phi_y = bsb ? pd.r : 0.f;
-    double pl = 0.0;
+    double pl = 0.0, pa = 0.0;
     for (int n = lane; n < pd.N; n += 32) {
         const size_t p = (size_t)n * pd.M + m;
         const float r = rbuf[p];
         pl += (double)r * (double)r;
-        alpha[p] = (n >= 1 ? 2.f * rbuf[p - pd.M] : 0.f) - 2.f * r * (1.f + phi_y * pd.dt);
+        const float a = (n >= 1 ? 2.f * rbuf[p - pd.M] : 0.f) - 2.f * r * (1.f + phi_y * pd.dt);
+        alpha[p] = a;
+        pa += (double)a;
     }
 #pragma unroll
-    for (int o = 16; o > 0; o >>= 1) pl += __shfl_xor_sync(0xffffffffu, pl, o);
+    for (int o = 16; o > 0; o >>= 1) {
+        pl += __shfl_xor_sync(0xffffffffu, pl, o);
+        pa += __shfl_xor_sync(0xffffffffu, pa, o);
+    }
     const float rprev = pd.N >= 1 ? rbuf[(size_t)(pd.N - 1) * pd.M + m] : 0.f;
     // terminal point n = N
     const size_t p = (size_t)pd.N * pd.M + m;
@@ -395,8 +411,10 @@ __global__ void k_seeds_paths(ProblemDev pd, const float* __restrict__ X, const 
     zt = warp_sum(zt);
     if (pd.tgt) pl += (double)zt;
     if (lane == 0) {
-        alpha[p] = (pd.N >= 1 ? 2.f * rprev : 0.f) + 2.f * rT;
+        const float a = (pd.N >= 1 ? 2.f * rprev : 0.f) + 2.f * rT;
+        alpha[p] = a;
         path_loss[m] = pl;
+        path_alpha[m] = pa + (double)a;
     }
 }
 
@@ -412,10 +430,11 @@ fbsde_status launch_seeds(fbsde_ctx* ctx, float* loss_dev, float* y0_dev) {
         FBSDE_CK_LAUNCH(ctx);
     }
     k_seeds_paths<<<(pd.M + wpb - 1) / wpb, 32 * wpb, 0, ctx->stream>>>(
-        pd, ctx->X, ctx->Y, ctx->Z, ctx->rbuf, ctx->alpha, V, ctx->path_loss_d, ctx->Vb_op, ctx->ld_op);
+        pd, ctx->X, ctx->Y, ctx->Z, ctx->rbuf, ctx->alpha, V, ctx->path_loss_d, ctx->path_loss_d + pd.M,
+        ctx->Vb_op, ctx->ld_op);
     FBSDE_CK_LAUNCH(ctx);
     k_loss_reduce<<<1, 1024, 0, ctx->stream>>>(ctx->path_loss_d, pd.M, ctx->Y, loss_dev, y0_dev,
-                                               ctx->nonfinite);
+                                               ctx->nonfinite, ctx->path_loss_d + pd.M, ctx->alpha_sum);
     prof_end(ctx, PROF_OTHER, tok, 0.0);
     FBSDE_CK_LAUNCH(ctx);
     return FBSDE_OK;

@@ -10,6 +10,7 @@
 #include <cuda_fp8.h>
 #include <cuda_runtime.h>
 
+#include <algorithm>
 #include <cstring>
 #include <string>
 
@@ -388,6 +389,32 @@ __global__ void k_cvt_bf16(int rows_o, int cols_o, int ldo, bf16* __restrict__ o
     out[(size_t)r * ldo + cc] = __float2bfloat16_rn(x);
 }
 
+// The BF16 weight copies refreshed every step, all in one launch
+// (blockIdx.y = copy): out[r][c] = S[r][off + c] (or S[c][off + r] when
+// transposed) for r < rows_v, c < cols_v, zero in the padding.
+struct CvtJob {
+    bf16* out;
+    const float* S;
+    int rows_o, cols_o, ldo, lds, off, rows_v, cols_v, tr;
+};
+constexpr int kMaxCvtJobs = 2 + 4 * kMaxDepth;
+struct CvtBatch {
+    CvtJob job[kMaxCvtJobs];
+    int n;
+};
+
+__global__ void k_cvt_bf16_batch(const __grid_constant__ CvtBatch b) {
+    const CvtJob& j = b.job[blockIdx.y];
+    const size_t n = (size_t)j.rows_o * j.cols_o;
+    for (size_t i = (size_t)blockIdx.x * blockDim.x + threadIdx.x; i < n; i += (size_t)gridDim.x * blockDim.x) {
+        const int r = (int)(i / j.cols_o), cc = (int)(i % j.cols_o);
+        float x = 0.f;
+        if (r < j.rows_v && cc < j.cols_v)
+            x = j.tr ? j.S[(size_t)cc * j.lds + j.off + r] : j.S[(size_t)r * j.lds + j.off + cc];
+        j.out[(size_t)r * j.ldo + cc] = __float2bfloat16_rn(x);
+    }
+}
+
 // g_L = w_o, e_L = c_L act'(a_L) w_o (BF16)
 __global__ void k_top_rev_b(size_t P, int w, int wp, const float* __restrict__ aL, const float* __restrict__ wo,
                             float cL, int act, float* __restrict__ gL, bf16* __restrict__ eL) {
@@ -684,11 +711,14 @@ fbsde_status bf16_prepare_weights(fbsde_ctx* c, const float* theta) {
     Bf16Work* b = c->bf;
     const int w = c->w, D = c->D, K0 = D + 1;
     const ParamLayout& pl = c->pl;
+    CvtBatch cb;
+    std::memset(&cb, 0, sizeof(cb));
+    size_t most = 0;
     auto cvt = [&](bf16* out, int rows_o, int cols_o, int ldo, const float* S, int lds, int off, int rows_v,
                    int cols_v, int tr) -> fbsde_status {
-        k_cvt_bf16<<<nblk((size_t)rows_o * cols_o, 256), 256, 0, c->stream>>>(rows_o, cols_o, ldo, out, S, lds, off,
-                                                                             rows_v, cols_v, tr);
-        FBSDE_CK_LAUNCH(c);
+        if (cb.n >= kMaxCvtJobs) return set_err(c, FBSDE_ERR_UNSUPPORTED, "too many weight copies");
+        cb.job[cb.n++] = CvtJob{out, S, rows_o, cols_o, ldo, lds, off, rows_v, cols_v, tr};
+        most = std::max(most, (size_t)rows_o * cols_o);
         return FBSDE_OK;
     };
     FBSDE_TRY(cvt(b->Winx, w, b->Dp, b->Dp, theta + pl.Win, K0, 1, w, D, 0));
@@ -702,6 +732,8 @@ fbsde_status bf16_prepare_weights(fbsde_ctx* c, const float* theta) {
             FBSDE_TRY(cvt(b->BxT[l], b->Dn, b->wp, b->wp, theta + pl.B[l], K0, 1, D, w, 1));
         }
     }
+    k_cvt_bf16_batch<<<dim3((unsigned)std::min<size_t>(nblk(most, 256), 64), (unsigned)cb.n), 256, 0, c->stream>>>(cb);
+    FBSDE_CK_LAUNCH(c);
     if (b->f8) {
         Fp8WeightArgs fa;
         std::memset(&fa, 0, sizeof(fa));
@@ -861,7 +893,8 @@ fbsde_status bf16_wgrad_tail(fbsde_ctx* c, const float* theta, float* grad) {
         FBSDE_TRY(colsum(c, PROF_WGRAD, b->Hf[L], false, w, w, 2, c->alpha, grad + pl.wo, 1, 0));
         FBSDE_TRY(colsum(c, PROF_WGRAD, b->HDf[L], false, w, w, 0, nullptr, grad + pl.wo, 1, 1));
     }
-    FBSDE_TRY(colsum(c, PROF_WGRAD, c->alpha, false, 1, 1, 0, nullptr, grad + pl.bo, 1, 0));
+    // db_o = sum_p alpha_p, formed with the loss (k_loss_reduce)
+    FBSDE_CK(c, cudaMemcpyAsync(grad + pl.bo, c->alpha_sum, sizeof(float), cudaMemcpyDeviceToDevice, c->stream));
     return launch_check_finite(c, grad, pl.total);
 }
 
