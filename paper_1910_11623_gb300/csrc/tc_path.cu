@@ -440,15 +440,35 @@ __global__ void k_top_adj_b(size_t P, int w, int wp, const float* __restrict__ a
 }
 
 // Partial column sums over a range of points, fixed order:
-// part[split][c] = sum_{p in split} wt(p) X[p][c], wt = 1 (mode 0), t_p (mode 1)
-// or wts[p] (mode 2).  256 threads: 32 column lanes x 8 row lanes; a column
+// part[split][c] = sum_{p in split} wt(p) X[p][c] (+ X2[p][c]), wt = 1 (mode 0),
+// t_p (mode 1) or wts[p] (mode 2); X2 (same layout, optional) enters with
+// weight 1.  256 threads: 32 column lanes x 8 row lanes; a column
 // lane covers 8 consecutive columns with one 16- or 32-byte load per row (the
 // vector path needs ncols and ldx multiples of 8), the row lanes stride the
 // split's rows and are combined in shared memory in a fixed order.
+// Eight consecutive values of a BF16 or FP32 row (16- or 32-byte aligned) as floats.
+template <class T>
+__device__ __forceinline__ void ld_row8(const T* src, float (&v)[8]) {
+    if (sizeof(T) == 2) {
+        const uint4 q = *reinterpret_cast<const uint4*>(src);
+        const uint32_t w4[4] = {q.x, q.y, q.z, q.w};
+#pragma unroll
+        for (int i = 0; i < 4; ++i) {
+            const float2 f = __bfloat1622float2(*reinterpret_cast<const __nv_bfloat162*>(&w4[i]));
+            v[2 * i] = f.x; v[2 * i + 1] = f.y;
+        }
+    } else {
+        const float4 a = reinterpret_cast<const float4*>(src)[0];
+        const float4 b = reinterpret_cast<const float4*>(src)[1];
+        v[0] = a.x; v[1] = a.y; v[2] = a.z; v[3] = a.w; v[4] = b.x; v[5] = b.y; v[6] = b.z; v[7] = b.w;
+    }
+}
+
 template <class T>
 __global__ void __launch_bounds__(256) k_colsum(size_t P, int ncols, const T* __restrict__ X, int ldx, int mode,
                                                 const float* __restrict__ wts, int M, float dt,
-                                                float* __restrict__ part, size_t chunk) {
+                                                float* __restrict__ part, size_t chunk,
+                                                const T* __restrict__ X2 = nullptr) {
     __shared__ float red[8][256 + 8];
     const int tx = threadIdx.x & 31, ty = threadIdx.x >> 5;
     const int split = blockIdx.x;
@@ -487,6 +507,15 @@ __global__ void __launch_bounds__(256) k_colsum(size_t P, int ncols, const T* __
 #pragma unroll
                     for (int i = 0; i < 8; ++i) acc[i] = fmaf(wt, v[u][i], acc[i]);
                 }
+                if (X2) {
+#pragma unroll
+                    for (int u = 0; u < 4; ++u) {
+                        float v2[8];
+                        ld_row8(X2 + (p + 8 * u) * ldx + c0, v2);
+#pragma unroll
+                        for (int i = 0; i < 8; ++i) acc[i] += v2[i];
+                    }
+                }
             }
             for (; p < p1; p += 8) {
                 const float wt = mode == 0 ? 1.f : mode == 1 ? (float)(p / M) * dt : wts[p];
@@ -507,6 +536,12 @@ __global__ void __launch_bounds__(256) k_colsum(size_t P, int ncols, const T* __
                 }
 #pragma unroll
                 for (int i = 0; i < 8; ++i) acc[i] = fmaf(wt, v[i], acc[i]);
+                if (X2) {
+                    float v2[8];
+                    ld_row8(X2 + p * ldx + c0, v2);
+#pragma unroll
+                    for (int i = 0; i < 8; ++i) acc[i] += v2[i];
+                }
             }
         } else if (!vec) {
             for (size_t p = p0 + ty; p < p1; p += 8) {
@@ -514,7 +549,10 @@ __global__ void __launch_bounds__(256) k_colsum(size_t P, int ncols, const T* __
                 const T* row = X + p * ldx;
 #pragma unroll
                 for (int i = 0; i < 8; ++i)
-                    if (c0 + i < ncols) acc[i] = fmaf(wt, (float)row[c0 + i], acc[i]);
+                    if (c0 + i < ncols) {
+                        acc[i] = fmaf(wt, (float)row[c0 + i], acc[i]);
+                        if (X2) acc[i] += (float)X2[p * ldx + c0 + i];
+                    }
             }
         }
 #pragma unroll
@@ -593,7 +631,7 @@ static void add_pair(TcArgs& a, const CUtensorMap& A, const CUtensorMap& B, int 
 }
 
 static fbsde_status colsum(fbsde_ctx* c, int cls, const void* X, bool is_bf16, int ldx, int ncols, int mode,
-                           const float* wts, float* out, int ldo, int accumulate) {
+                           const float* wts, float* out, int ldo, int accumulate, const void* X2 = nullptr) {
     Bf16Work* b = c->bf;
     const size_t P = c->P();
     const size_t chunk = (P + kColSplits - 1) / kColSplits;
@@ -601,9 +639,11 @@ static fbsde_status colsum(fbsde_ctx* c, int cls, const void* X, bool is_bf16, i
     const float dt = (float)(c->T / c->N);
     const int tok = prof_begin(c, cls);
     if (is_bf16)
-        k_colsum<bf16><<<splits, 256, 0, c->stream>>>(P, ncols, (const bf16*)X, ldx, mode, wts, c->M, dt, b->colpart, chunk);
+        k_colsum<bf16><<<splits, 256, 0, c->stream>>>(P, ncols, (const bf16*)X, ldx, mode, wts, c->M, dt, b->colpart,
+                                                       chunk, (const bf16*)X2);
     else
-        k_colsum<float><<<splits, 256, 0, c->stream>>>(P, ncols, (const float*)X, ldx, mode, wts, c->M, dt, b->colpart, chunk);
+        k_colsum<float><<<splits, 256, 0, c->stream>>>(P, ncols, (const float*)X, ldx, mode, wts, c->M, dt, b->colpart,
+                                                        chunk, (const float*)X2);
     FBSDE_CK_LAUNCH(c);
     k_colsum_reduce<<<nblk((size_t)ncols * 32, 256), 256, 0, c->stream>>>(b->colpart, splits, ncols, out, ldo,
                                                                         accumulate);
@@ -887,11 +927,9 @@ fbsde_status bf16_wgrad_tail(fbsde_ctx* c, const float* theta, float* grad) {
     }
     // dw_o = sum_p alpha_p h_L(p) + h'_L(p);  db_o = sum_p alpha_p
     if (b->fused) {
-        FBSDE_TRY(colsum(c, PROF_WGRAD, b->Hb[L], true, wp, w, 2, c->alpha, grad + pl.wo, 1, 0));
-        FBSDE_TRY(colsum(c, PROF_WGRAD, b->HDb[L], true, wp, w, 0, nullptr, grad + pl.wo, 1, 1));
+        FBSDE_TRY(colsum(c, PROF_WGRAD, b->Hb[L], true, wp, w, 2, c->alpha, grad + pl.wo, 1, 0, b->HDb[L]));
     } else {
-        FBSDE_TRY(colsum(c, PROF_WGRAD, b->Hf[L], false, w, w, 2, c->alpha, grad + pl.wo, 1, 0));
-        FBSDE_TRY(colsum(c, PROF_WGRAD, b->HDf[L], false, w, w, 0, nullptr, grad + pl.wo, 1, 1));
+        FBSDE_TRY(colsum(c, PROF_WGRAD, b->Hf[L], false, w, w, 2, c->alpha, grad + pl.wo, 1, 0, b->HDf[L]));
     }
     // db_o = sum_p alpha_p, formed with the loss (k_loss_reduce)
     FBSDE_CK(c, cudaMemcpyAsync(grad + pl.bo, c->alpha_sum, sizeof(float), cudaMemcpyDeviceToDevice, c->stream));
