@@ -55,6 +55,7 @@ constexpr int kFusedMaxDepth = 8;  // depth served by the per-tile fused kernels
 
 struct Bf16Work {
     int Dp, Dn, wp;  // D padded to 64 (operand rows), D padded to 16 (MMA N), w padded to 64
+    int sms = 1;     // multiprocessors of the device
     void* mem = nullptr;
     bf16 *Xb, *Vb;
     bf16 *Hb[kMaxDepth + 1], *Eb[kMaxDepth + 1], *HDb[kMaxDepth + 1], *ABb[kMaxDepth + 1];

@@ -116,11 +116,14 @@ fbsde_status bf16_create(fbsde_ctx* c) {
                        "that is a multiple of 32");
     b->wp8 = (int)rup(w, 128);
     c->need_V32 = !b->fused;  // the fused backward reads the BF16 v rows only
-    if (b->fused) {
+    {
         int dev = 0, sms = 0;
         FBSDE_CK(c, cudaGetDevice(&dev));
         FBSDE_CK(c, cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev));
-        b->grid = sms;
+        b->sms = sms > 0 ? sms : 1;
+    }
+    if (b->fused) {
+        b->grid = b->sms;
         b->G_stride = rup((Pm + 127) / 128 * 128 * (size_t)w, 128);
     }
     // the layered sweeps keep FP32 copies of every per-layer tensor; the fused
@@ -661,7 +664,10 @@ static fbsde_status wgrad(fbsde_ctx* c, TcArgs a, int ncols_store, float* out, i
                           float* cs_out = nullptr, int cs_ld = 1, float* cst_out = nullptr, int cst_ld = 1) {
     const size_t P = c->P();
     const int mblocks = (a.rows + 127) / 128;
-    int want = (2 * 148 + mblocks - 1) / mblocks;
+    // one wave of CTAs (one per SM, each streaming its own range of points):
+    // half the split-K partials of two waves, and measured faster than both
+    // two waves and half a wave
+    int want = (c->bf->sms + mblocks - 1) / mblocks;
     size_t kc = rup((P + want - 1) / want, 64);
     int splits = (int)((P + kc - 1) / kc);
     while ((size_t)splits * a.rows * a.N > c->part_floats) {
