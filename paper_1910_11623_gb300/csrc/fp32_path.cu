@@ -219,9 +219,9 @@ __global__ void k_proj_scales(int n, const WxwArgs a, float delta, float* __rest
     const int l = blockIdx.x + 1;
     const float* __restrict__ G = a.C[l];
     __shared__ double sh[1024];
-    double acc = 0.0;
-    for (int i = threadIdx.x; i < n; i += blockDim.x) acc += (double)G[i] * (double)G[i];
-    sh[threadIdx.x] = acc;
+    float part = 0.f;  // a thread's n / 1024 squares in FP32, the tree in FP64
+    for (int i = threadIdx.x; i < n; i += blockDim.x) part = fmaf(G[i], G[i], part);
+    sh[threadIdx.x] = (double)part;
     __syncthreads();
     for (int s = blockDim.x / 2; s > 0; s >>= 1) {
         if (threadIdx.x < s) sh[threadIdx.x] += sh[threadIdx.x + s];

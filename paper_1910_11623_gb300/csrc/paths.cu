@@ -51,6 +51,9 @@ __global__ void k_paths(ProblemDev pd, const float* __restrict__ x0, uint32_t k0
     };
     put(X ? X + (size_t)m * pd.D + d0 : nullptr, Xb ? Xb + (size_t)m * ldb + d0 : nullptr, x);
     const float sqrt2 = 1.41421356237309515f;
+    // the draws of later steps do not depend on X: unrolled, their Philox
+    // rounds overlap the X updates and stores of earlier ones
+#pragma unroll 4
     for (int n = 0; n < pd.N; ++n) {
         u32x4 c{(uint32_t)q, (uint32_t)n, (uint32_t)m, it};
         u32x4 w = philox4x32_10(c, k0, k1);
@@ -312,9 +315,14 @@ __global__ void k_resid(ProblemDev pd, const float* __restrict__ X, const float*
         }
     };
     float zx = 0.f, zsdw = 0.f, zz = 0.f;
+    float x0[4], z0[4], w0[4];  // this lane's first quad, kept for the second pass
     for (int q = lane; q < Q; q += 32) {
         float xv[4], zv[4], dw[4];
         quad(q, xv, zv, dw);
+        if (q == lane) {
+#pragma unroll
+            for (int j = 0; j < 4; ++j) { x0[j] = xv[j]; z0[j] = zv[j]; w0[j] = dw[j]; }
+        }
 #pragma unroll
         for (int j = 0; j < 4; ++j) {  // padded dimensions carry x = z = 0
             const float sdw = bsb ? pd.sigma * xv[j] * dw[j] : sqrt2 * dw[j];
@@ -330,7 +338,12 @@ __global__ void k_resid(ProblemDev pd, const float* __restrict__ X, const float*
     if (lane == 0) rbuf[p] = r;
     for (int q = lane; q < Q; q += 32) {
         float xv[4], zv[4], dw[4], v[4];
-        quad(q, xv, zv, dw);
+        if (q == lane) {
+#pragma unroll
+            for (int j = 0; j < 4; ++j) { xv[j] = x0[j]; zv[j] = z0[j]; dw[j] = w0[j]; }
+        } else {
+            quad(q, xv, zv, dw);
+        }
 #pragma unroll
         for (int j = 0; j < 4; ++j) {
             const float sdw = bsb ? pd.sigma * xv[j] * dw[j] : sqrt2 * dw[j];
