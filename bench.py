@@ -55,6 +55,9 @@ def parse_args():
                     help="Adam steps of the FP8-hidden-layer form (timed for speed, then trained; 0: skip)")
     ap.add_argument("--nais-steps", type=int, default=5,
                     help="timed steps of the HJB NAIS-Net workload in both forms (0: skip)")
+    ap.add_argument("--nais-accuracy-steps", type=int, default=0,
+                    help="> 0: also train the NAIS-Net HJB workload (BF16) until |Y0 - u(0,0)| <= 1%% "
+                         "(at most this many steps)")
     ap.add_argument("--wide-steps", type=int, default=3,
                     help="train steps timed per form on the NAIS-Net 6 x 512 network (BSB, M = 16384); 0 skips")
     ap.add_argument("--wide-accuracy-steps", type=int, default=0,
@@ -635,6 +638,10 @@ def main():
                 sn.close()
                 torch.cuda.empty_cache()
             res_n["speedup_bf16_vs_fp32"] = res_n["bf16"]["value"] / res_n["fp32"]["value"]
+            if args.nais_accuracy_steps > 0:
+                # u(0, 0) of the HJB problem by Cole-Hopf (chi-square quadrature)
+                res_n["accuracy"] = single_level_run(P, wn.with_prec("bf16"), P.workloads.HJB_U00_D100,
+                                                     args.nais_accuracy_steps)
             out["nais_hjb"] = res_n
         except Exception as exc:
             out["nais_hjb"] = {"error": f"{type(exc).__name__}: {exc}"}
