@@ -8,6 +8,7 @@ sizes used for measurement.  This module holds specifications only.
 """
 from __future__ import annotations
 
+import math
 from dataclasses import dataclass, replace
 
 from .solver import ArchSpec, ProblemSpec
@@ -58,15 +59,14 @@ WORKLOADS = {
 
 # Closed-form anchors (Section 4): BSB u(0, x0) and HJB u(0, 0) (Cole-Hopf,
 # chi-square quadrature), used for the accuracy of a trained Y_0.
-BSB_Y0_D100 = 77.10487946
-BSB_Y0_D10 = 7.710487946
+BSB_Y0_D100 = 62.5 * math.exp(0.21)  # ||x0||^2 = 62.5, (r + sigma^2) T = 0.21
+BSB_Y0_D10 = 6.25 * math.exp(0.21)
 HJB_U00_D100 = 4.590162
 
 
 def bsb_y0(x0, r: float = 0.05, sigma: float = 0.4, T: float = 1.0) -> float:
     """Closed form of the BSB problem (Section 4.1) at t = 0:
     u(0, x) = exp((r + sigma^2) T) ||x||^2."""
-    import math
     return math.exp((r + sigma * sigma) * T) * sum(float(v) * float(v) for v in x0)
 
 
