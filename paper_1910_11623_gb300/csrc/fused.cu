@@ -1,17 +1,17 @@
-// Per-tile fused kernels of the BF16 form (FC and ResNet networks).
+// Per-tile fused kernels of the BF16 form (FC, ResNet and NAIS-Net networks).
 //
 // Both kernels walk one tile of 128 points (persistent CTAs, one per SM)
 // through a fixed sequence of layer contractions without leaving the SM:
 //   * activation tiles (BF16, 128 rows x up to 256 columns) live in shared
 //     memory in the 128-byte-swizzled K-major layout the tensor cores read,
 //     and each layer's epilogue rewrites them in place;
-//   * the forward kernel keeps the ResNet residual stream (FP32) in TMEM
-//     columns 256..511 next to the accumulator (columns 0..255); the
-//     backward kernel holds two accumulators there (forward recomputation
-//     and tangent) and accumulates the adjoint h-bar in place;
+//   * the forward kernel keeps the residual stream (FP32) in TMEM columns
+//     256..511 next to the accumulator (columns 0..255); the backward kernel
+//     holds two accumulators there (forward recomputation and tangent) and
+//     accumulates the adjoint h-bar in place;
 //   * the weights stream from L2 through a TMA ring, one 64-wide K slice per
-//     stage, in the order the layers consume them, so the next layer's
-//     weights arrive while the current epilogue runs;
+//     stage, in the order the layers consume them (NAIS-Net blocks: then the
+//     B_l slices, each beside this tile's input rows in the next stage);
 //   * per-layer derivatives needed later in the tile go to a per-CTA scratch
 //     region that the same CTA reads back within microseconds.
 // Warp 0 issues the weight TMA loads and warp 1 allocates TMEM and issues
@@ -975,9 +975,9 @@ __global__ void __launch_bounds__(bwd_threads(), 1) k_fused_bwd(const __grid_con
         const int row = lg * 32 + lane;
         const uint32_t tacc = tmem + ((uint32_t)(lg * 32) << 16);
         const uint32_t tsec = tacc + 256u;  // tangent accumulator in the up-sweep, hbar in the down-sweep
-        // per-column parameters (biases, w_o, W_in[:,0]): 16-byte broadcast
-        // loads from a small table in global memory; the shared memory holds
-        // a third weight stage instead
+        // per-column parameters (biases, w_o, W_in[:,0]; NAIS-Net: B_l[:,0]):
+        // 16-byte broadcast loads from the table staged in shared memory at
+        // the start (copied from the table k_stage_pvec forms each step)
         const float* wo = ptab + (size_t)(L + 1) * a.w;
         const float* win0 = ptab + (size_t)(L + 2) * a.w;
         const size_t blk = (size_t)(a.w / 2) * 128;
