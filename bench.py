@@ -224,10 +224,12 @@ def time_steps(solver, theta, m, v, first_step, K, lr):
 
 def batched_run(P, steps: int, lr: float):
     """32 independent uneven instances (half BSB, half HJB; D, N, M, width
-    drawn with a seed) trained together: each instance's training step on
-    its own stream, the group step captured as one CUDA graph, the SM split
-    between the instances autotuned.  Against: the same instances trained
-    one after another with direct calls."""
+    drawn with a seed) trained together, the group step captured as one CUDA
+    graph and the SM split between the instances autotuned, in both group
+    modes: grouped launches (the fused instances' forward and backward
+    kernels as one launch each) and streams (every instance's step on its own
+    stream).  Against: the same instances trained one after another with
+    direct calls."""
     import torch
     from paper_1910_11623_gb300 import _lib as L
     ws = P.workloads.batched_instances()
@@ -257,25 +259,31 @@ def batched_run(P, steps: int, lr: float):
         per.append(e0.elapsed_time(e1) / steps)
     seq_ms = sum(per)
     G = P.Group(solvers)
-    caps, tune_ms, _ = G.autotune(th, lr, trial_steps=1)
-    step_dev = torch.full((n,), 2 + steps, dtype=torch.int64, device="cuda")
-    graph = G.capture(th, mm, vv, step_dev, lr, steps=1)
-    graph.launch()
-    torch.cuda.synchronize()
-    e0.record(G.stream)
-    for _ in range(steps):
+    modes = {}
+    for mode in ("grouped", "streams"):
+        G.set_mode(mode)
+        caps, tune_ms, _ = G.autotune(th, lr, trial_steps=1)
+        step_dev = torch.full((n,), 2 + steps, dtype=torch.int64, device="cuda")
+        graph = G.capture(th, mm, vv, step_dev, lr, steps=1)
         graph.launch()
-    e1.record(G.stream)
-    e1.synchronize()
-    g_ms = e0.elapsed_time(e1) / steps
+        torch.cuda.synchronize()
+        e0.record(G.stream)
+        for _ in range(steps):
+            graph.launch()
+        e1.record(G.stream)
+        e1.synchronize()
+        modes[mode] = {"ms_per_round": e0.elapsed_time(e1) / steps,
+                       "autotune": {"caps": caps, "ms_per_step": tune_ms}}
+        graph.close()
+    g_ms = modes["grouped"]["ms_per_round"]
     pts = sum(w.problem.M * (w.problem.N + 1) for w in ws)
     res = {"instances": n, "points_per_round": pts,
            "shapes": [[w.problem.kind, w.problem.D, w.problem.N, w.problem.M, w.arch.width] for w in ws],
            "sequential_ms_per_round": seq_ms, "grouped_ms_per_round": g_ms,
+           "streams_ms_per_round": modes["streams"]["ms_per_round"],
            "speedup_grouped_vs_sequential": seq_ms / g_ms,
-           "instance_steps_per_s": n / (g_ms / 1000.0), "autotune": {"caps": caps, "ms_per_step": tune_ms},
+           "instance_steps_per_s": n / (g_ms / 1000.0), "modes": modes,
            "timing": f"{steps} group steps replayed from one CUDA graph per step, after one warm replay"}
-    graph.close()
     G.close()
     for s in solvers:
         s.close()

@@ -244,9 +244,21 @@ fbsde_status fbsde_graph_destroy(fbsde_graph* graph);
  * fbsde_group_train_step: one training step of every instance (as
  * fbsde_train_step_dev): theta, m, v are n device pointers (host array),
  * step_dev a device array of n uint64 step counters, loss_dev / y0_dev NULL
- * or device arrays of n floats (instance i writes index i).  The instances
- * run concurrently on their streams; on return the group's stream is ordered
- * after all of them.
+ * or device arrays of n floats (instance i writes index i).  On return the
+ * group's stream is ordered after all of them.  In FBSDE_GROUP_GROUPED mode
+ * (the default) the instances served by the fused BF16 kernels with the same
+ * kernel variant (activation and network kind; FP8 forms excluded), when
+ * there are at least two, run their forward kernels as one persistent launch
+ * and their backward kernels as one more, instance i on its own range of
+ * CTAs (its grid cap, one per SM when unset); their other kernels, and every
+ * other instance's whole step, run on the instances' streams.  The launch
+ * arguments live in device memory owned by the group and are re-uploaded
+ * (with a synchronisation of the group's stream) only when they change, e.g.
+ * when theta pointers change.  In FBSDE_GROUP_STREAMS mode every instance
+ * runs its whole step on its own stream, concurrently.
+ *
+ * fbsde_group_set_mode: FBSDE_GROUP_GROUPED or FBSDE_GROUP_STREAMS
+ * (FBSDE_ERR_INVALID otherwise).
  *
  * fbsde_group_capture: `steps` group steps captured on the group's stream as
  * one CUDA graph (fbsde_graph_launch replays it with a single launch).
@@ -263,6 +275,7 @@ fbsde_status fbsde_graph_destroy(fbsde_graph* graph);
  * and the step time in ms to *ms_out (may be NULL).  Synchronises the group's
  * stream; the caller's theta is only read. */
 typedef struct fbsde_group fbsde_group;
+enum { FBSDE_GROUP_STREAMS = 0, FBSDE_GROUP_GROUPED = 1 };
 /* A new non-blocking CUDA stream (cudaStream_t in *out), for callers whose
  * framework hands out pooled streams, so that every instance of a group can
  * have one of its own; fbsde_stream_destroy frees it (NULL accepted). */
@@ -270,6 +283,7 @@ fbsde_status fbsde_stream_create(void** out);
 fbsde_status fbsde_stream_destroy(void* stream);
 fbsde_status fbsde_group_create(fbsde_ctx* const* ctxs, int n, void* cuda_stream, fbsde_group** out);
 fbsde_status fbsde_group_destroy(fbsde_group* group);
+fbsde_status fbsde_group_set_mode(fbsde_group* group, int mode);
 fbsde_status fbsde_group_train_step(fbsde_group* group, float* const* theta_dev, float* const* adam_m_dev,
                                     float* const* adam_v_dev, uint64_t* step_dev, float lr, float* loss_dev,
                                     float* y0_dev);

@@ -19,6 +19,7 @@ FBSDE_BSB, FBSDE_HJB = 0, 1
 FBSDE_FC, FBSDE_RESNET, FBSDE_NAIS = 0, 1, 2
 FBSDE_SIN, FBSDE_TANH = 0, 1
 FBSDE_FP32, FBSDE_BF16, FBSDE_FP8_HIDDEN = 0, 1, 2
+FBSDE_GROUP_STREAMS, FBSDE_GROUP_GROUPED = 0, 1
 
 
 class fbsde_problem(ctypes.Structure):
@@ -57,6 +58,7 @@ SIGNATURES = {
     "fbsde_graph_launch": (c_int, [c_void_p]),
     "fbsde_group_create": (c_int, [POINTER(c_void_p), c_int, c_void_p, POINTER(c_void_p)]),
     "fbsde_group_destroy": (c_int, [c_void_p]),
+    "fbsde_group_set_mode": (c_int, [c_void_p, c_int]),
     "fbsde_group_train_step": (c_int, [c_void_p, POINTER(c_void_p), POINTER(c_void_p), POINTER(c_void_p),
                                        c_void_p, c_float, c_void_p, c_void_p]),
     "fbsde_group_capture": (c_int, [c_void_p, POINTER(c_void_p), POINTER(c_void_p), POINTER(c_void_p),
@@ -230,6 +232,10 @@ def fbsde_group_create(ctxs, stream: int):
 
 def fbsde_group_destroy(group):
     load().fbsde_group_destroy(group)
+
+
+def fbsde_group_set_mode(group, mode: int):
+    check(load().fbsde_group_set_mode(group, mode), "fbsde_group_set_mode")
 
 
 def fbsde_group_train_step(group, theta_ptrs, m_ptrs, v_ptrs, step_ptr: int, lr: float, loss_ptr: int = 0,

@@ -102,6 +102,30 @@ __host__ __device__ inline float e4m3_act_scale(int l, bool res) {
 
 fbsde_status fused_forward(fbsde_ctx* c, const float* theta, bool for_grad);
 fbsde_status fused_backward(fbsde_ctx* c, const float* theta);
+
+// One launch of each fused kernel for several instances (a group) that share
+// the kernel variant: instance i takes its CTA count from its grid cap (one
+// per SM when unset), and its arguments are uploaded to `dev` by
+// fused_group_prepare (a blocking copy, only when they changed; while a graph
+// is being captured they must already be in place).
+struct FusedGroupBuf {
+    void* host = nullptr;  // argument block being built
+    void* last = nullptr;  // the block the device copy holds
+    void* dev = nullptr;
+    size_t bytes = 0;
+    size_t smem_fwd = 0, smem_bwd = 0;
+    int cap = 0, n = 0, grid = 0;
+    bool valid = false;
+};
+int fused_variant(const fbsde_ctx* c);
+bool fused_groupable(const fbsde_ctx* c);
+fbsde_status fused_group_alloc(FusedGroupBuf* g, int n);
+void fused_group_free(FusedGroupBuf* g);
+fbsde_status fused_group_prepare(fbsde_ctx* const* c, const float* const* theta, int n, FusedGroupBuf* g,
+                                 cudaStream_t st);
+fbsde_status fused_group_forward(fbsde_ctx* const* c, int n, FusedGroupBuf* g, cudaStream_t st);
+fbsde_status fused_group_stage_pvec(fbsde_ctx* c, const float* theta, cudaStream_t st);
+fbsde_status fused_group_backward(fbsde_ctx* const* c, int n, FusedGroupBuf* g, cudaStream_t st);
 fbsde_status bf16_wgrad_tail(fbsde_ctx* c, const float* theta, float* grad);
 
 }  // namespace fbsde

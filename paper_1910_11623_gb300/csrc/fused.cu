@@ -36,6 +36,8 @@
 #include <cuda_fp8.h>
 #include <cuda_runtime.h>
 
+#include <algorithm>
+#include <cstdlib>
 #include <cstring>
 #include <string>
 
@@ -373,7 +375,7 @@ __device__ void producer_role(const Sched& sch, int ntiles, int nstages, uint8_t
                               uint64_t* bempty, volatile int* abort_flag, int* err) {
     int it = 0;
     bool ok = true;
-    for (int t = blockIdx.x; t < ntiles && ok; t += gridDim.x) {
+    for (int t = sch.cta; t < ntiles && ok; t += sch.nctas) {
         for (int q = 0; q < sch.nq() && ok; ++q) {
             const FGemm g = sch.gemm(q);
             const int nload = XS ? g.nk + 2 * g.nx + g.nk2 : g.nk;
@@ -419,7 +421,7 @@ __device__ void mma_role(const Sched& sch, int ntiles, int nstages, uint32_t aba
                          uint64_t* aready, volatile int* abort_flag, int* err) {
     int it = 0, qg = 0;
     bool ok = true;
-    for (int t = blockIdx.x; t < ntiles && ok; t += gridDim.x) {
+    for (int t = sch.cta; t < ntiles && ok; t += sch.nctas) {
         for (int q = 0; q < sch.nq() && ok; ++q, ++qg) {
             if (*abort_flag || !tc::mbar_wait(aready, (uint32_t)qg & 1u, tc::kWaitBudget)) {
                 ok = false;
@@ -540,6 +542,7 @@ struct FwdZArgs {
 
 struct FwdZSched {
     const FwdZArgs* a;
+    int cta, nctas;  // this CTA among the CTAs that share the tiles
     __device__ int nq() const { return 2 * a->L + 2; }
     // 0: lift, 1..L: layers, L+1..2L: reverse through layer 2L+1-q, 2L+1: Z
     __device__ FGemm gemm(int q) const {
@@ -575,14 +578,15 @@ struct FwdZSched {
         if (q > L && q <= 2 * L) {
             const int l = 2 * L + 1 - q;
             const size_t blk = (size_t)(a->w / 2) * 128;
-            tc::prefetch_l2_bulk(a->scratch + ((size_t)blockIdx.x * L + (l - 1)) * blk, (uint32_t)(blk * 4));
+            tc::prefetch_l2_bulk(a->scratch + ((size_t)cta * L + (l - 1)) * blk, (uint32_t)(blk * 4));
         }
     }
 };
 
-// NAIS: NAIS-Net blocks (h_l = h_{l-1} + h act(A_l h_{l-1} + B_l u + C_l), Section 3.1)
+// NAIS: NAIS-Net blocks (h_l = h_{l-1} + h act(A_l h_{l-1} + B_l u + C_l), Section 3.1).
+// The CTA is number `cta` of the `nctas` CTAs that walk this instance's tiles.
 template <int ACT, bool RES, bool F8, bool NAIS>
-__global__ void __launch_bounds__(fused_threads(kFwdGroups), 1) k_fused_fwdz(const __grid_constant__ FwdZArgs a) {
+__device__ __forceinline__ void fwdz_body(const FwdZArgs& a, const int cta, const int nctas) {
     constexpr int NG = kFwdGroups, NE = 128 * NG;
     extern __shared__ uint8_t smem_raw[];
     uint8_t* smem = (uint8_t*)(((uintptr_t)smem_raw + 1023) & ~(uintptr_t)1023);
@@ -604,7 +608,7 @@ __global__ void __launch_bounds__(fused_threads(kFwdGroups), 1) k_fused_fwdz(con
 
     const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
     const int L = a.L;
-    const FwdZSched sch{&a};
+    const FwdZSched sch{&a, cta, nctas};
 
     stage_params(ptab, a.theta, a.off, L, a.w, a.D + 1);
     if (threadIdx.x == 0) {
@@ -645,7 +649,7 @@ __global__ void __launch_bounds__(fused_threads(kFwdGroups), 1) k_fused_fwdz(con
         const float* wo = ptab + (L + 1) * a.w;
         const float* win0 = ptab + (L + 2) * a.w;
         const size_t blk = (size_t)(a.w / 2) * 128;  // words of one column-pair-major 128-row block
-        uint32_t* scr = a.scratch + (size_t)blockIdx.x * L * blk;
+        uint32_t* scr = a.scratch + (size_t)cta * L * blk;
         StoreSync ss{tfree, wdone, warp == 2 && lane == 0, 0u, 0u};
         // L2 policies: per-CTA scratch stays (re-read within microseconds),
         // the g_l / e_l streams go out first (read by later kernels)
@@ -666,7 +670,7 @@ __global__ void __launch_bounds__(fused_threads(kFwdGroups), 1) k_fused_fwdz(con
             }
         };
         bool requested = false;
-        for (int t = blockIdx.x; t < a.ntiles && ok; t += gridDim.x) {
+        for (int t = cta; t < a.ntiles && ok; t += nctas) {
             const int p = t * 128 + row;
             const bool valid = p < a.P;
             const float tval = valid ? (float)(p / a.M) * a.dt : 0.f;
@@ -687,9 +691,9 @@ __global__ void __launch_bounds__(fused_threads(kFwdGroups), 1) k_fused_fwdz(con
                 tc::tc_fence_after();
                 const bool writes_tile = q <= 2 * L;
                 if (writes_tile && !ss.before_write()) { ok = false; break; }
-                if (q == nq - 1 && t + (int)gridDim.x < a.ntiles) {
+                if (q == nq - 1 && t + nctas < a.ntiles) {
                     if (!ss.before_write()) { ok = false; break; }
-                    request_x(t + (int)gridDim.x);
+                    request_x(t + nctas);
                     requested = true;
                 }
                 int store_layer = -1;  // e_l stored from the tile after this phase
@@ -836,6 +840,22 @@ __global__ void __launch_bounds__(fused_threads(kFwdGroups), 1) k_fused_fwdz(con
     }
 }
 
+template <int ACT, bool RES, bool F8, bool NAIS>
+__global__ void __launch_bounds__(fused_threads(kFwdGroups), 1) k_fused_fwdz(const __grid_constant__ FwdZArgs a) {
+    fwdz_body<ACT, RES, F8, NAIS>(a, (int)blockIdx.x, (int)gridDim.x);
+}
+
+// One launch for the forward kernels of several instances (a group): CTAs
+// cta_begin[i] .. cta_begin[i+1]-1 walk the tiles of instance i, whose
+// arguments (tensor maps included) sit in global memory.
+template <int ACT, bool RES, bool F8, bool NAIS>
+__global__ void __launch_bounds__(fused_threads(kFwdGroups), 1)
+    k_fused_fwdz_group(const FwdZArgs* __restrict__ all, const int* __restrict__ cta_begin, int n) {
+    int i = 0;
+    while (i + 1 < n && (int)blockIdx.x >= cta_begin[i + 1]) ++i;
+    fwdz_body<ACT, RES, F8, NAIS>(all[i], (int)blockIdx.x - cta_begin[i], cta_begin[i + 1] - cta_begin[i]);
+}
+
 // ---------------------------------------------------------------- tangent + adjoint
 
 struct BwdArgs {
@@ -863,6 +883,7 @@ struct BwdArgs {
 
 struct BwdSched {
     const BwdArgs* a;
+    int cta, nctas;  // this CTA among the CTAs that share the tiles
     __device__ int nq() const { return 2 * a->L + 1; }
     // l = q (0..L): forward and tangent contractions of layer l together (two
     // accumulators, one weight stream); q = L+1+j: adjoint through layer L-j
@@ -901,7 +922,7 @@ struct BwdSched {
             tc::prefetch_l2_bulk(a->G + (size_t)q * a->G_words + (size_t)t * blk, (uint32_t)(blk * 4));
         } else if (q > L) {
             const int l = L - (q - (L + 1));
-            const uint32_t* d1 = a->scratch + (size_t)blockIdx.x * 2 * L * blk + (size_t)(l - 1) * blk;
+            const uint32_t* d1 = a->scratch + (size_t)cta * 2 * L * blk + (size_t)(l - 1) * blk;
             tc::prefetch_l2_bulk(d1, (uint32_t)(blk * 4));
             tc::prefetch_l2_bulk(d1 + (size_t)L * blk, (uint32_t)(blk * 4));
         }
@@ -912,7 +933,7 @@ struct BwdSched {
 // FP32 residual of k_fused_fwdz has no room here: TMEM holds both the forward
 // and the tangent accumulators), and carries the tangent h' in BF16 as well.
 template <int ACT, bool RES, bool NAIS>
-__global__ void __launch_bounds__(bwd_threads(), 1) k_fused_bwd(const __grid_constant__ BwdArgs a) {
+__device__ __forceinline__ void bwd_body(const BwdArgs& a, const int cta, const int nctas) {
     constexpr int NG = kBwdGroups, NE = 128 * NG;
     extern __shared__ uint8_t smem_raw[];
     uint8_t* smem = (uint8_t*)(((uintptr_t)smem_raw + 1023) & ~(uintptr_t)1023);
@@ -933,7 +954,7 @@ __global__ void __launch_bounds__(bwd_threads(), 1) k_fused_bwd(const __grid_con
 
     const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
     const int L = a.L;
-    const BwdSched sch{&a};
+    const BwdSched sch{&a, cta, nctas};
 
     for (int k = threadIdx.x; k < prows * a.w / 4; k += blockDim.x)
         reinterpret_cast<float4*>(ptab)[k] = __ldg(reinterpret_cast<const float4*>(a.pvec) + k);
@@ -981,7 +1002,7 @@ __global__ void __launch_bounds__(bwd_threads(), 1) k_fused_bwd(const __grid_con
         const float* wo = ptab + (size_t)(L + 1) * a.w;
         const float* win0 = ptab + (size_t)(L + 2) * a.w;
         const size_t blk = (size_t)(a.w / 2) * 128;
-        uint32_t* scr_d1 = a.scratch + (size_t)blockIdx.x * 2 * L * blk;  // act'(a_l), l < L
+        uint32_t* scr_d1 = a.scratch + (size_t)cta * 2 * L * blk;  // act'(a_l), l < L
         uint32_t* scr_S = scr_d1 + (size_t)L * blk;                       // S_l, l < L
         StoreSync ss{tfree, wdone, warp == 4 && lane == 0, 0u, 0u};
         // L2 policies: per-CTA scratch stays (re-read within microseconds),
@@ -997,7 +1018,7 @@ __global__ void __launch_bounds__(bwd_threads(), 1) k_fused_bwd(const __grid_con
         // goes through the phase (the named barriers of the slab stores need
         // every epilogue thread); at the end of each phase all of them take
         // the same decision, so none is left waiting at a barrier.
-        for (int t = blockIdx.x; t < a.ntiles && ok; t += gridDim.x) {
+        for (int t = cta; t < a.ntiles && ok; t += nctas) {
             const int p = t * 128 + row;
             const bool valid = p < a.P;
             const float tval = valid ? (float)(p / a.M) * a.dt : 0.f;
@@ -1022,13 +1043,13 @@ __global__ void __launch_bounds__(bwd_threads(), 1) k_fused_bwd(const __grid_con
                 if (ok) ok = tc::mbar_wait(accf, (uint32_t)qg & 1u, tc::kWaitBudget);
                 tc::tc_fence_after();
                 if (ok) ok = ss.before_write();
-                if (q == L + 1 && t + (int)gridDim.x < a.ntiles) {
+                if (q == L + 1 && t + nctas < a.ntiles) {
                     // the last reader of tile_d was the dual contraction of
                     // layer L and its stores have drained (before_write)
                     if (ss.st_thread) {
                         tc::mbar_expect_tx_only(xfull, (uint32_t)nkx * 16384u);
                         for (int k = 0; k < nkx; ++k)
-                            tc::tma_load_2d(tile_d + k * 16384, &a.vb, xfull, k * 64, (t + (int)gridDim.x) * 128);
+                            tc::tma_load_2d(tile_d + k * 16384, &a.vb, xfull, k * 64, (t + nctas) * 128);
                     }
                     v_requested = true;
                 }
@@ -1170,6 +1191,20 @@ __global__ void __launch_bounds__(bwd_threads(), 1) k_fused_bwd(const __grid_con
     }
 }
 
+template <int ACT, bool RES, bool NAIS>
+__global__ void __launch_bounds__(bwd_threads(), 1) k_fused_bwd(const __grid_constant__ BwdArgs a) {
+    bwd_body<ACT, RES, NAIS>(a, (int)blockIdx.x, (int)gridDim.x);
+}
+
+// The backward kernels of a group in one launch (as k_fused_fwdz_group).
+template <int ACT, bool RES, bool NAIS>
+__global__ void __launch_bounds__(bwd_threads(), 1)
+    k_fused_bwd_group(const BwdArgs* __restrict__ all, const int* __restrict__ cta_begin, int n) {
+    int i = 0;
+    while (i + 1 < n && (int)blockIdx.x >= cta_begin[i + 1]) ++i;
+    bwd_body<ACT, RES, NAIS>(all[i], (int)blockIdx.x - cta_begin[i], cta_begin[i + 1] - cta_begin[i]);
+}
+
 // ---------------------------------------------------------------- host launchers
 
 static size_t fwdz_smem_bytes(int L, int w, int nais) {
@@ -1210,9 +1245,9 @@ static ParamOffsets param_offsets(const fbsde_ctx* c) {
     return o;
 }
 
-fbsde_status fused_forward(fbsde_ctx* c, const float* theta, bool for_grad) {
+// Arguments of one instance's forward kernel.
+static void fwd_args(fbsde_ctx* c, const float* theta, bool for_grad, FwdZArgs& a) {
     Bf16Work* b = c->bf;
-    FwdZArgs a;
     std::memset(&a, 0, sizeof(a));
     a.wf[0] = b->mWinx;
     a.wr[0] = b->mWinxT;
@@ -1239,6 +1274,13 @@ fbsde_status fused_forward(fbsde_ctx* c, const float* theta, bool for_grad) {
         for (int l = 1; l <= c->L; ++l) a.wbxT[l] = b->mBxT[l];
         a.hs = (float)c->h;
     }
+}
+
+fbsde_status fused_forward(fbsde_ctx* c, const float* theta, bool for_grad) {
+    Bf16Work* b = c->bf;
+    FwdZArgs a;
+    fwd_args(c, theta, for_grad, a);
+    const bool nais = c->akind == FBSDE_NAIS;
     const int cap = c->grid_cap > 0 && c->grid_cap < b->grid ? c->grid_cap : b->grid;
     const int grid = a.ntiles < cap ? a.ntiles : cap;
     const size_t smem = fwdz_smem_bytes(c->L, c->w, nais ? 1 : 0);
@@ -1281,9 +1323,9 @@ __global__ void k_stage_pvec(const float* __restrict__ th, ParamOffsets o, int L
         pvec[i] = param_value(th, o, L, i / w, i % w, K0);
 }
 
-fbsde_status fused_backward(fbsde_ctx* c, const float* theta) {
+// Arguments of one instance's backward kernel.
+static void bwd_args(fbsde_ctx* c, const float* theta, BwdArgs& a) {
     Bf16Work* b = c->bf;
-    BwdArgs a;
     std::memset(&a, 0, sizeof(a));
     a.wf[0] = b->mWinx;
     for (int l = 1; l <= c->L; ++l) {
@@ -1305,12 +1347,24 @@ fbsde_status fused_backward(fbsde_ctx* c, const float* theta) {
         for (int l = 1; l <= c->L; ++l) a.wbx[l] = b->mBx[l];
         a.hs = (float)c->h;
     }
-    k_stage_pvec<<<4, 256, 0, c->stream>>>(theta, a.off, c->L, c->w, c->D + 1, b->pvec);
-    {
-        cudaError_t le = cudaGetLastError();
-        if (le != cudaSuccess) return set_err(c, FBSDE_ERR_CUDA, std::string("parameter table: ") + cudaGetErrorString(le));
-        ++c->n_launch;
-    }
+}
+
+// The per-column parameter table of the backward, from Theta (one small launch).
+static fbsde_status stage_pvec(fbsde_ctx* c, const float* theta, cudaStream_t st) {
+    const ParamOffsets off = param_offsets(c);
+    k_stage_pvec<<<4, 256, 0, st>>>(theta, off, c->L, c->w, c->D + 1, c->bf->pvec);
+    cudaError_t le = cudaGetLastError();
+    if (le != cudaSuccess) return set_err(c, FBSDE_ERR_CUDA, std::string("parameter table: ") + cudaGetErrorString(le));
+    ++c->n_launch;
+    return FBSDE_OK;
+}
+
+fbsde_status fused_backward(fbsde_ctx* c, const float* theta) {
+    Bf16Work* b = c->bf;
+    BwdArgs a;
+    bwd_args(c, theta, a);
+    const bool nais = c->akind == FBSDE_NAIS;
+    FBSDE_TRY(stage_pvec(c, theta, c->stream));
     const int cap = c->grid_cap > 0 && c->grid_cap < b->grid ? c->grid_cap : b->grid;
     const int grid = a.ntiles < cap ? a.ntiles : cap;
     const size_t smem = bwd_smem_bytes(c->L, c->w, nais ? 1 : 0);
@@ -1333,6 +1387,143 @@ fbsde_status fused_backward(fbsde_ctx* c, const float* theta) {
     prof_end(c, PROF_POINTS, tok, 2.0 * P * w * (D + 2.0 * c->L * w + (nais ? c->L * D : 0.0)));
     if (e != cudaSuccess) return set_err(c, FBSDE_ERR_CUDA, std::string("fused backward: ") + cudaGetErrorString(e));
     ++c->n_launch;
+    return FBSDE_OK;
+}
+
+// ---------------------------------------------------------------- grouped launches
+
+// Kernel variant of an instance (activation x network kind); instances of one
+// grouped launch share it.
+int fused_variant(const fbsde_ctx* c) {
+    return (c->act == FBSDE_TANH ? 1 : 0) | (c->akind == FBSDE_RESNET ? 2 : c->akind == FBSDE_NAIS ? 4 : 0);
+}
+
+bool fused_groupable(const fbsde_ctx* c) {
+    return c->prec != FBSDE_FP32 && c->bf && c->bf->fused && !c->bf->f8;
+}
+
+fbsde_status fused_group_alloc(FusedGroupBuf* g, int n) {
+    fused_group_free(g);
+    g->bytes = (size_t)n * (sizeof(FwdZArgs) + sizeof(BwdArgs)) + (size_t)(n + 1) * sizeof(int);
+    g->host = std::malloc(g->bytes);
+    g->last = std::malloc(g->bytes);
+    if (!g->host || !g->last || cudaMalloc(&g->dev, g->bytes) != cudaSuccess) {
+        fused_group_free(g);
+        return FBSDE_ERR_OOM;
+    }
+    g->cap = n;
+    g->valid = false;
+    return FBSDE_OK;
+}
+
+void fused_group_free(FusedGroupBuf* g) {
+    std::free(g->host);
+    std::free(g->last);
+    if (g->dev) cudaFree(g->dev);
+    g->host = g->last = nullptr;
+    g->dev = nullptr;
+    g->cap = 0;
+    g->valid = false;
+}
+
+// Layout of the argument block: n forward arguments, n backward arguments
+// (both 64-byte aligned: they hold tensor maps), then the n + 1 CTA offsets.
+static FwdZArgs* fwd_block(void* base) { return reinterpret_cast<FwdZArgs*>(base); }
+static BwdArgs* bwd_block(void* base, int cap) {
+    return reinterpret_cast<BwdArgs*>(static_cast<char*>(base) + (size_t)cap * sizeof(FwdZArgs));
+}
+static int* begin_block(void* base, int cap) {
+    return reinterpret_cast<int*>(static_cast<char*>(base) + (size_t)cap * (sizeof(FwdZArgs) + sizeof(BwdArgs)));
+}
+
+fbsde_status fused_group_prepare(fbsde_ctx* const* c, const float* const* theta, int n, FusedGroupBuf* g,
+                                 cudaStream_t st) {
+    if (n < 1 || n > g->cap) return FBSDE_ERR_INVALID;
+    std::memset(g->host, 0, g->bytes);
+    FwdZArgs* fa = fwd_block(g->host);
+    BwdArgs* ba = bwd_block(g->host, g->cap);
+    int* beg = begin_block(g->host, g->cap);
+    beg[0] = 0;
+    g->smem_fwd = g->smem_bwd = 0;
+    for (int i = 0; i < n; ++i) {
+        fwd_args(c[i], theta[i], true, fa[i]);
+        bwd_args(c[i], theta[i], ba[i]);
+        const int cap = c[i]->grid_cap > 0 && c[i]->grid_cap < c[i]->bf->grid ? c[i]->grid_cap : c[i]->bf->grid;
+        beg[i + 1] = beg[i] + std::max(1, std::min(cap, fa[i].ntiles));
+        const int nais = c[i]->akind == FBSDE_NAIS ? 1 : 0;
+        g->smem_fwd = std::max(g->smem_fwd, fwdz_smem_bytes(c[i]->L, c[i]->w, nais));
+        g->smem_bwd = std::max(g->smem_bwd, bwd_smem_bytes(c[i]->L, c[i]->w, nais));
+    }
+    g->n = n;
+    g->grid = beg[n];
+    if (g->valid && std::memcmp(g->host, g->last, g->bytes) == 0) return FBSDE_OK;
+    // new arguments: the device copy must not change under a launch in
+    // flight, and a graph being captured must find it already in place
+    cudaStreamCaptureStatus cs = cudaStreamCaptureStatusNone;
+    if (cudaStreamIsCapturing(st, &cs) != cudaSuccess) return FBSDE_ERR_CUDA;
+    if (cs != cudaStreamCaptureStatusNone) return FBSDE_ERR_UNSUPPORTED;
+    if (cudaStreamSynchronize(st) != cudaSuccess ||
+        cudaMemcpy(g->dev, g->host, g->bytes, cudaMemcpyHostToDevice) != cudaSuccess)
+        return FBSDE_ERR_CUDA;
+    std::memcpy(g->last, g->host, g->bytes);
+    g->valid = true;
+    return FBSDE_OK;
+}
+
+template <class K, class A>
+static cudaError_t launch_group(K kernel, const A* all, const int* beg, int n, int grid, int threads, size_t smem,
+                                cudaStream_t st, int launch_regs) {
+    cudaError_t e = cudaFuncSetAttribute(kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+    if (e != cudaSuccess) return e;
+    if (launch_regs > 0) {
+        cudaFuncAttributes fa;
+        e = cudaFuncGetAttributes(&fa, kernel);
+        if (e != cudaSuccess) return e;
+        if (fa.numRegs != launch_regs || fa.maxThreadsPerBlock < threads) return cudaErrorInvalidConfiguration;
+    }
+    kernel<<<grid, threads, smem, st>>>(all, beg, n);
+    return cudaGetLastError();
+}
+
+fbsde_status fused_group_forward(fbsde_ctx* const* c, int n, FusedGroupBuf* g, cudaStream_t st) {
+    if (n != g->n || !g->valid) return FBSDE_ERR_INVALID;
+    const FwdZArgs* all = fwd_block(g->dev);
+    const int* beg = begin_block(g->dev, g->cap);
+    const int FT = fused_threads(kFwdGroups);
+    cudaError_t e;
+    switch (fused_variant(c[0])) {
+        case 0: e = launch_group(k_fused_fwdz_group<FBSDE_SIN, false, false, false>, all, beg, n, g->grid, FT, g->smem_fwd, st, 0); break;
+        case 1: e = launch_group(k_fused_fwdz_group<FBSDE_TANH, false, false, false>, all, beg, n, g->grid, FT, g->smem_fwd, st, 0); break;
+        case 2: e = launch_group(k_fused_fwdz_group<FBSDE_SIN, true, false, false>, all, beg, n, g->grid, FT, g->smem_fwd, st, 0); break;
+        case 3: e = launch_group(k_fused_fwdz_group<FBSDE_TANH, true, false, false>, all, beg, n, g->grid, FT, g->smem_fwd, st, 0); break;
+        case 4: e = launch_group(k_fused_fwdz_group<FBSDE_SIN, true, false, true>, all, beg, n, g->grid, FT, g->smem_fwd, st, 0); break;
+        default: e = launch_group(k_fused_fwdz_group<FBSDE_TANH, true, false, true>, all, beg, n, g->grid, FT, g->smem_fwd, st, 0); break;
+    }
+    if (e != cudaSuccess) return set_err(c[0], FBSDE_ERR_CUDA, std::string("grouped fused forward: ") + cudaGetErrorString(e));
+    ++c[0]->n_launch;
+    return FBSDE_OK;
+}
+
+fbsde_status fused_group_stage_pvec(fbsde_ctx* c, const float* theta, cudaStream_t st) {
+    return stage_pvec(c, theta, st);
+}
+
+fbsde_status fused_group_backward(fbsde_ctx* const* c, int n, FusedGroupBuf* g, cudaStream_t st) {
+    if (n != g->n || !g->valid) return FBSDE_ERR_INVALID;
+    const BwdArgs* all = bwd_block(g->dev, g->cap);
+    const int* beg = begin_block(g->dev, g->cap);
+    const int FT = bwd_threads(), R = kBwdRegsLaunch;
+    cudaError_t e;
+    switch (fused_variant(c[0])) {
+        case 0: e = launch_group(k_fused_bwd_group<FBSDE_SIN, false, false>, all, beg, n, g->grid, FT, g->smem_bwd, st, R); break;
+        case 1: e = launch_group(k_fused_bwd_group<FBSDE_TANH, false, false>, all, beg, n, g->grid, FT, g->smem_bwd, st, R); break;
+        case 2: e = launch_group(k_fused_bwd_group<FBSDE_SIN, true, false>, all, beg, n, g->grid, FT, g->smem_bwd, st, R); break;
+        case 3: e = launch_group(k_fused_bwd_group<FBSDE_TANH, true, false>, all, beg, n, g->grid, FT, g->smem_bwd, st, R); break;
+        case 4: e = launch_group(k_fused_bwd_group<FBSDE_SIN, true, true>, all, beg, n, g->grid, FT, g->smem_bwd, st, R); break;
+        default: e = launch_group(k_fused_bwd_group<FBSDE_TANH, true, true>, all, beg, n, g->grid, FT, g->smem_bwd, st, R); break;
+    }
+    if (e != cudaSuccess) return set_err(c[0], FBSDE_ERR_CUDA, std::string("grouped fused backward: ") + cudaGetErrorString(e));
+    ++c[0]->n_launch;
     return FBSDE_OK;
 }
 

@@ -1,15 +1,21 @@
 // Groups of independent FBSDE instances trained together (many problems of
 // uneven D, N, M and width at once).  Each instance keeps its own context,
-// stream and workspace; a group step forks from the group's stream to every
-// instance's stream, enqueues that instance's whole training step (device
-// step counter) there, and joins back, so the instances' kernels run
-// concurrently and the whole group step can be captured as one CUDA graph
-// and replayed with a single launch.
+// stream and workspace; the group step can be captured as one CUDA graph and
+// replayed with a single launch.  Two ways to run a step:
 //
-// The fused per-tile kernels of an instance normally take every SM; in a
-// group the instances share the SMs.  The autotuner times candidate splits
-// of the SMs between the instances (each instance's cap on its fused-kernel
-// CTAs) on scratch copies of the training state and keeps the fastest.
+//   * grouped launches (default): the instances served by the fused BF16
+//     kernels with a common kernel variant run their forward kernels as ONE
+//     persistent launch and their backward kernels as one more (CTA ranges
+//     per instance, each walking its own tiles); the per-instance steps
+//     around them (paths, weights, residuals, weight gradients, Adam) run on
+//     the instances' streams between fork and join events.  Other instances
+//     run whole steps on their own streams alongside.
+//   * streams: every instance's whole step on its own stream, concurrently.
+//
+// The fused kernels of an instance alone take every SM; in a group the
+// instances share them.  The autotuner times candidate splits (each
+// instance's CTA count) on scratch copies of the training state and keeps
+// the fastest.
 #include <cuda_runtime.h>
 
 #include <algorithm>
@@ -19,30 +25,120 @@
 #include <vector>
 
 #include "internal.cuh"
+#include "bf16_work.cuh"
 
 using namespace fbsde;
 
 struct fbsde_group {
     std::vector<fbsde_ctx*> ctx;
     cudaStream_t stream = nullptr;
-    cudaEvent_t fork = nullptr;
+    cudaEvent_t fork = nullptr, fork2 = nullptr, fork3 = nullptr;
     std::vector<cudaEvent_t> join;
     int sms = 0;
+    int mode = FBSDE_GROUP_GROUPED;
+    FusedGroupBuf buf;
 };
 
 namespace {
 
+#define GCK(call)                                              \
+    do {                                                       \
+        if ((call) != cudaSuccess) return FBSDE_ERR_CUDA;      \
+    } while (0)
+
+// instances whose fused kernels go into the grouped launches: fused BF16
+// instances of the first such instance's kernel variant (at least two)
+std::vector<int> grouped_members(const fbsde_group* g) {
+    std::vector<int> gi;
+    int variant = -1;
+    for (size_t i = 0; i < g->ctx.size(); ++i) {
+        const fbsde_ctx* c = g->ctx[i];
+        if (!fused_groupable(c)) continue;
+        if (variant < 0) variant = fused_variant(c);
+        if (fused_variant(c) == variant) gi.push_back((int)i);
+    }
+    if (g->mode != FBSDE_GROUP_GROUPED || gi.size() < 2) gi.clear();
+    return gi;
+}
+
+// the arguments of the grouped launches, uploaded when they changed
+fbsde_status group_prepare(fbsde_group* g, const std::vector<int>& gi, float* const* theta) {
+    if (gi.empty()) return FBSDE_OK;
+    std::vector<fbsde_ctx*> gc;
+    std::vector<const float*> gt;
+    for (int i : gi) {
+        gc.push_back(g->ctx[i]);
+        gt.push_back(theta[i]);
+    }
+    if (g->buf.cap < (int)gi.size()) FBSDE_TRY(fused_group_alloc(&g->buf, (int)g->ctx.size()));
+    return fused_group_prepare(gc.data(), gt.data(), (int)gi.size(), &g->buf, g->stream);
+}
+
 fbsde_status group_enqueue(fbsde_group* g, float* const* theta, float* const* m, float* const* v,
                            uint64_t* step_dev, float lr, float* loss_dev, float* y0_dev) {
-    if (cudaEventRecord(g->fork, g->stream) != cudaSuccess) return FBSDE_ERR_CUDA;
-    for (size_t i = 0; i < g->ctx.size(); ++i) {
+    const int n = (int)g->ctx.size();
+    const std::vector<int> gi = grouped_members(g);
+    std::vector<char> in_group(n, 0);
+    for (int i : gi) in_group[i] = 1;
+    FBSDE_TRY(group_prepare(g, gi, theta));
+    GCK(cudaEventRecord(g->fork, g->stream));
+    // whole steps on the instances' own streams
+    for (int i = 0; i < n; ++i) {
+        if (in_group[i]) continue;
         fbsde_ctx* c = g->ctx[i];
-        if (cudaStreamWaitEvent(c->stream, g->fork, 0) != cudaSuccess) return FBSDE_ERR_CUDA;
+        GCK(cudaStreamWaitEvent(c->stream, g->fork, 0));
         FBSDE_TRY(fbsde_train_step_dev(c, theta[i], m[i], v[i], step_dev + i, lr,
                                        loss_dev ? loss_dev + i : nullptr, y0_dev ? y0_dev + i : nullptr));
-        if (cudaEventRecord(g->join[i], c->stream) != cudaSuccess) return FBSDE_ERR_CUDA;
-        if (cudaStreamWaitEvent(g->stream, g->join[i], 0) != cudaSuccess) return FBSDE_ERR_CUDA;
+        GCK(cudaEventRecord(g->join[i], c->stream));
     }
+    if (!gi.empty()) {
+        std::vector<fbsde_ctx*> gc;
+        for (int i : gi) gc.push_back(g->ctx[i]);
+        const int ng = (int)gi.size();
+        // each stage runs per instance on its stream between fork and join
+        // events around the grouped launches on the group's stream
+        auto stage = [&](cudaEvent_t after, auto&& body) -> fbsde_status {
+            for (int i : gi) {
+                fbsde_ctx* c = g->ctx[i];
+                GCK(cudaStreamWaitEvent(c->stream, after, 0));
+                c->step_dev = step_dev + i;
+                const fbsde_status st = body(i, c);
+                c->step_dev = nullptr;
+                FBSDE_TRY(st);
+                GCK(cudaEventRecord(g->join[i], c->stream));
+                GCK(cudaStreamWaitEvent(g->stream, g->join[i], 0));
+            }
+            return FBSDE_OK;
+        };
+        // paths and BF16 weights; then every forward kernel in one launch
+        FBSDE_TRY(stage(g->fork, [&](int i, fbsde_ctx* c) -> fbsde_status {
+            FBSDE_TRY(launch_paths(c, 1));
+            return bf16_prepare_weights(c, theta[i]);
+        }));
+        FBSDE_TRY(fused_group_forward(gc.data(), ng, &g->buf, g->stream));
+        GCK(cudaEventRecord(g->fork2, g->stream));
+        // residuals, loss and seeds, the backward's parameter table; then
+        // every backward kernel in one launch
+        FBSDE_TRY(stage(g->fork2, [&](int i, fbsde_ctx* c) -> fbsde_status {
+            FBSDE_TRY(launch_seeds(c, loss_dev ? loss_dev + i : nullptr, y0_dev ? y0_dev + i : nullptr));
+            return fused_group_stage_pvec(c, theta[i], c->stream);
+        }));
+        FBSDE_TRY(fused_group_backward(gc.data(), ng, &g->buf, g->stream));
+        GCK(cudaEventRecord(g->fork3, g->stream));
+        // weight gradients, Adam (device step), NAIS-Net projection, next step
+        FBSDE_TRY(stage(g->fork3, [&](int i, fbsde_ctx* c) -> fbsde_status {
+            FBSDE_TRY(bf16_wgrad_tail(c, theta[i], c->gradbuf));
+            FBSDE_TRY(launch_adam(c, theta[i], c->gradbuf, m[i], v[i], 1, lr));
+            if (c->akind == FBSDE_NAIS) FBSDE_TRY(nais_project(c, theta[i]));
+            return FBSDE_OK;
+        }));
+        for (int i : gi) {
+            fbsde_ctx* c = g->ctx[i];
+            FBSDE_TRY(launch_step_advance(c, step_dev + i));
+            GCK(cudaEventRecord(g->join[i], c->stream));
+        }
+    }
+    for (int i = 0; i < n; ++i) GCK(cudaStreamWaitEvent(g->stream, g->join[i], 0));
     return FBSDE_OK;
 }
 
@@ -86,7 +182,9 @@ fbsde_status fbsde_group_create(fbsde_ctx* const* ctxs, int n, void* cuda_stream
     int dev = 0;
     bool ok = cudaGetDevice(&dev) == cudaSuccess &&
               cudaDeviceGetAttribute(&g->sms, cudaDevAttrMultiProcessorCount, dev) == cudaSuccess &&
-              cudaEventCreateWithFlags(&g->fork, cudaEventDisableTiming) == cudaSuccess;
+              cudaEventCreateWithFlags(&g->fork, cudaEventDisableTiming) == cudaSuccess &&
+              cudaEventCreateWithFlags(&g->fork2, cudaEventDisableTiming) == cudaSuccess &&
+              cudaEventCreateWithFlags(&g->fork3, cudaEventDisableTiming) == cudaSuccess;
     g->join.assign(n, nullptr);
     for (int i = 0; ok && i < n; ++i) ok = cudaEventCreateWithFlags(&g->join[i], cudaEventDisableTiming) == cudaSuccess;
     if (!ok) {
@@ -99,10 +197,20 @@ fbsde_status fbsde_group_create(fbsde_ctx* const* ctxs, int n, void* cuda_stream
 
 fbsde_status fbsde_group_destroy(fbsde_group* g) {
     if (!g) return FBSDE_OK;
+    if (g->stream) cudaStreamSynchronize(g->stream);
+    fused_group_free(&g->buf);
     if (g->fork) cudaEventDestroy(g->fork);
+    if (g->fork2) cudaEventDestroy(g->fork2);
+    if (g->fork3) cudaEventDestroy(g->fork3);
     for (cudaEvent_t e : g->join)
         if (e) cudaEventDestroy(e);
     delete g;
+    return FBSDE_OK;
+}
+
+fbsde_status fbsde_group_set_mode(fbsde_group* g, int mode) {
+    if (!g || (mode != FBSDE_GROUP_STREAMS && mode != FBSDE_GROUP_GROUPED)) return FBSDE_ERR_INVALID;
+    g->mode = mode;
     return FBSDE_OK;
 }
 
@@ -120,6 +228,8 @@ fbsde_status fbsde_group_capture(fbsde_group* g, float* const* theta, float* con
     if (!g || !theta || !m || !v || !step_dev || steps < 1) return FBSDE_ERR_INVALID;
     for (fbsde_ctx* c : g->ctx)
         if (c->prof.on) return set_err(c, FBSDE_ERR_INVALID, "disable profiling before capturing a graph");
+    // the grouped launches' arguments go to the device before the capture
+    FBSDE_TRY(group_prepare(g, grouped_members(g), theta));
     if (cudaStreamBeginCapture(g->stream, cudaStreamCaptureModeThreadLocal) != cudaSuccess) return FBSDE_ERR_CUDA;
     fbsde_status st = FBSDE_OK;
     for (int k = 0; k < steps && st == FBSDE_OK; ++k) st = group_enqueue(g, theta, m, v, step_dev, lr, loss_dev, y0_dev);

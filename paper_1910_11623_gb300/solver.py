@@ -102,8 +102,16 @@ class Solver:
             raise ValueError(f"expected a contiguous CUDA float32 tensor of {self.n_params} entries")
 
     def init_params(self) -> torch.Tensor:
+        """Theta_0 (Xavier; NAIS-Net blocks projected), written on the solver's
+        stream; the caller's current stream is ordered after it, so the tensor
+        can be used (or copied) there at once.  The other methods enqueue on
+        the solver's stream only: run them under torch.cuda.stream(solver.stream)
+        or order the streams yourself."""
+        cur = torch.cuda.current_stream(self.device)
         theta = torch.empty(self.n_params, device=self.device)
+        self.stream.wait_stream(cur)
         L.fbsde_init_params(self.ctx, theta.data_ptr())
+        cur.wait_stream(self.stream)
         return theta
 
     def rollout_loss(self, theta: torch.Tensor, iteration: int):
@@ -235,9 +243,11 @@ class TrainGraph:
 
 class Group:
     """Independent instances (each a Solver on its own stream) trained
-    together: one group step runs every instance's training step
-    concurrently, capture() makes it one CUDA graph, autotune() splits the
-    SMs between the instances (cached per set of shapes in a JSON file)."""
+    together: one group step trains every instance (the fused BF16 ones of a
+    common kernel variant through one grouped forward and one grouped
+    backward launch, mode "grouped"; or every step on its own stream, mode
+    "streams"), capture() makes it one CUDA graph, autotune() splits the SMs
+    between the instances (cached per set of shapes in a JSON file)."""
 
     def __init__(self, solvers, stream: Optional[torch.cuda.Stream] = None):
         self.solvers = list(solvers)
@@ -249,6 +259,11 @@ class Group:
 
     def _ptrs(self, ts):
         return [t.data_ptr() for t in ts]
+
+    def set_mode(self, mode: str):
+        """"grouped" (default) or "streams"."""
+        L.fbsde_group_set_mode(self.handle, {"streams": L.FBSDE_GROUP_STREAMS,
+                                             "grouped": L.FBSDE_GROUP_GROUPED}[mode])
 
     def train_step(self, thetas, ms, vs, step_dev, lr: float = 1e-3):
         L.fbsde_group_train_step(self.handle, self._ptrs(thetas), self._ptrs(ms), self._ptrs(vs),

@@ -374,6 +374,55 @@ def test_group_of_uneven_instances(P, tmp_path):
     G.close()
 
 
+@pytest.mark.parametrize("kind", ["resnet", "nais"])
+def test_grouped_launch_matches_solo(P, kind):
+    # instances of one kernel variant but uneven D, N, M, width and depth
+    # share one grouped forward and one grouped backward launch per step
+    # (CTA ranges from the autotuned split); an instance of another variant
+    # and an FP32 one run whole steps on their own streams alongside.  Every
+    # instance ends exactly where it ends trained alone.
+    h = 0.5 if kind == "nais" else 1.0
+    specs = [
+        (P.ProblemSpec(kind="bsb", D=6, N=4, M=32, x0=[1.0, 0.5] * 3),
+         P.ArchSpec(kind=kind, width=32, depth=2, act="tanh", h=h, prec="bf16")),
+        (P.ProblemSpec(kind="hjb", D=13, N=7, M=37, x0=[0.0] * 13),
+         P.ArchSpec(kind=kind, width=48, depth=3, act="tanh", h=h, prec="bf16")),
+        (P.ProblemSpec(kind="bsb", D=100, N=16, M=64, x0=P.workloads.bsb_x0(100)),
+         P.ArchSpec(kind=kind, width=256, depth=5, act="tanh", h=h, prec="bf16")),
+        (P.ProblemSpec(kind="hjb", D=5, N=3, M=20, x0=[0.0] * 5),
+         P.ArchSpec(kind="fc", width=32, depth=2, act="sin", prec="bf16")),
+        (P.ProblemSpec(kind="bsb", D=4, N=8, M=16, x0=[1.0] * 4),
+         P.ArchSpec(kind="resnet", width=16, depth=1, act="tanh", prec="fp32")),
+    ]
+    solo, grouped = [], []
+    for k, (prob, arch) in enumerate(specs):
+        s = P.Solver(prob, arch, seed=20 + k, stream=torch.cuda.Stream())
+        th = s.init_params()
+        solo.append((s, th.clone(), torch.zeros_like(th), torch.zeros_like(th)))
+        s2 = P.Solver(prob, arch, seed=20 + k, stream=torch.cuda.Stream())
+        grouped.append((s2, th.clone(), torch.zeros_like(th), torch.zeros_like(th)))
+    for s, th, m, v in solo:
+        with torch.cuda.stream(s.stream):
+            for step in range(1, 5):
+                s.train_step(th, m, v, step, 1e-3)
+        s.stream.synchronize()
+    G = P.Group([g[0] for g in grouped])
+    ths, ms, vs = [g[1] for g in grouped], [g[2] for g in grouped], [g[3] for g in grouped]
+    G.autotune(ths, trial_steps=1)
+    step_dev = torch.ones(len(specs), dtype=torch.int64, device="cuda")
+    with torch.cuda.stream(G.stream):
+        G.train_step(ths, ms, vs, step_dev, 1e-3)
+        G.train_step(ths, ms, vs, step_dev, 1e-3)
+        graph = G.capture(ths, ms, vs, step_dev, 1e-3, steps=2)
+        graph.launch()
+    G.stream.synchronize()
+    assert step_dev.tolist() == [5] * len(specs)
+    for k, ((s, th, m, v), (_, thg, mg, vg)) in enumerate(zip(solo, grouped)):
+        assert torch.equal(th, thg) and torch.equal(m, mg) and torch.equal(v, vg), k
+    graph.close()
+    G.close()
+
+
 def test_bf16_many_point_splits_width128(P):
     # enough points that the weight-gradient contraction splits K into its
     # full number of chunks at width 128 (column sums of every split kept)
