@@ -130,3 +130,4 @@ def test_group_entry_points_reject_bad_arguments_without_a_gpu(L):
     assert lib.fbsde_group_destroy(None) == L.FBSDE_OK
     assert lib.fbsde_group_train_step(None, None, None, None, None, 1e-3, None, None) == L.FBSDE_ERR_INVALID
     assert lib.fbsde_set_grid_cap(None, 0) == L.FBSDE_ERR_INVALID
+    assert lib.fbsde_group_set_mode(None, L.FBSDE_GROUP_GROUPED) == L.FBSDE_ERR_INVALID
