@@ -32,7 +32,8 @@
 namespace fbsde {
 
 constexpr int kTcStages = 4;
-constexpr int kTcMaxPairs = 2;
+// operand pairs one contraction can sum (the NAIS-Net Z contraction takes L + 1)
+constexpr int kTcMaxPairs = 17;
 
 struct TcPair {
     CUtensorMap a;  // NT: [rows x K], box {64, 128}; TN: [K x rows], box {64, 64}

@@ -838,17 +838,12 @@ fbsde_status bf16_forward(fbsde_ctx* c, const float* theta, bool for_grad) {
                   act};
         FBSDE_TRY(tc_launch<false>(c, PROF_POINTS, a, 1, e, 2.0 * P * w * (double)w));
     }
-    {   // Z = W_in[:,1:]^T e_0 (+ sum_l B_l[:,1:]^T e_l)
+    {   // Z = W_in[:,1:]^T e_0 (+ sum_l B_l[:,1:]^T e_l): one contraction over all pairs
         TcArgs a = nt_args(c, P, b->Dn);
         add_pair(a, b->mEb[0], b->mWinxT, w);
-        FBSDE_TRY(tc_launch<false>(c, PROF_POINTS, a, 1, EpiZB{c->Z, D, 0}, 2.0 * P * D * (double)w));
-        if (nais) {
-            for (int l = 1; l <= L; ++l) {
-                TcArgs an = nt_args(c, P, b->Dn);
-                add_pair(an, b->mEb[l], b->mBxT[l], w);
-                FBSDE_TRY(tc_launch<false>(c, PROF_POINTS, an, 1, EpiZB{c->Z, D, 1}, 2.0 * P * D * (double)w));
-            }
-        }
+        if (nais)
+            for (int l = 1; l <= L; ++l) add_pair(a, b->mEb[l], b->mBxT[l], w);
+        FBSDE_TRY(tc_launch<false>(c, PROF_POINTS, a, 1, EpiZB{c->Z, D, 0}, 2.0 * P * D * (double)w * a.npairs));
     }
     return FBSDE_OK;
 }
