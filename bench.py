@@ -166,6 +166,23 @@ def ncu_traffic(form: str, workload: str):
     return d.get("dram_bytes_per_launch")
 
 
+def fused_algorithmic_bytes(w):
+    """Bytes one fused forward and one fused backward launch must move (their
+    mean), or None when the workload is not served by the fused kernels.
+    Forward: the e_l (L + 1) and g_l (L) BF16 operand blocks, Z and Y written,
+    the BF16 X rows read.  Backward: h'_l, h_l and abar_l (3 (L + 1) blocks)
+    written, the g_l blocks and the BF16 X and v rows read."""
+    p, a = w.problem, w.arch
+    if a.prec == "fp32" or a.width > 256 or a.depth > 8 or p.D > 256:
+        return None
+    P, L = p.M * (p.N + 1), a.depth
+    stack = P * (-(-a.width // 64) * 64) * 2
+    rows = P * (-(-p.D // 64) * 64) * 2
+    fwd = (2 * L + 1) * stack + rows + P * p.D * 4 + P * 4
+    bwd = 3 * (L + 1) * stack + L * stack + 2 * rows
+    return (fwd + bwd) / 2.0
+
+
 # ----------------------------------------------------------------- CPU oracle
 
 def cpu_oracle_rate(workload, sample_paths: int, iters: int):
@@ -496,6 +513,14 @@ def main():
             bound, unit = "alu", "TFLOP/s"
             achieved = dfl / (dms / 1000.0) / 1e12 if dms > 0 else None
         traffic = ncu_traffic(args.form, args.workload)
+        # the same kernels against HBM: the algorithmic bytes of a launch over
+        # its measured duration
+        hbm_view = None
+        ab = fused_algorithmic_bytes(w)
+        if ab and dom == 0 and dms > 0 and dn > 0:
+            gbs = ab / (dms / dn / 1000.0) / 1e9
+            hbm_view = {"algorithmic_bytes_per_launch": ab, "achieved_gbs": gbs, "peak_gbs": peaks["hbm_gbs"],
+                        "frac": gbs / peaks["hbm_gbs"]}
         out = {
             "metric": METRIC, "value": value, "unit": "it/s", "n_gpus": world,
             "steps": timed_steps, "warmup": args.warmup, "ms_per_step": ms_max / timed_steps,
@@ -513,7 +538,7 @@ def main():
                          "frac": (achieved / peak) if achieved else None,
                          "traffic": traffic,
                          "kernel": ["point contractions", "weight-gradient contractions"][dom],
-                         "launches": dn, "ms_total": dms, "flops_total": dfl,
+                         "launches": dn, "ms_total": dms, "flops_total": dfl, "hbm_view": hbm_view,
                          "peak_source": (peak_src + (" sustained bf16" if args.form == "bf16"
                                                      else " FP32 FFMA from SM count and max clock"))},
             "kernel_classes": {name: {"ms": p[0], "launches": p[1], "flops": p[2]}
