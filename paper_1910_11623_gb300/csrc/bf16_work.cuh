@@ -59,8 +59,10 @@ struct Bf16Work {
     void* mem = nullptr;
     bf16 *Xb, *Vb;
     bf16 *Hb[kMaxDepth + 1], *Eb[kMaxDepth + 1], *HDb[kMaxDepth + 1], *ABb[kMaxDepth + 1];
-    float *Af[kMaxDepth + 1], *Hf[kMaxDepth + 1], *Gf[kMaxDepth + 1], *HDf[kMaxDepth + 1];
-    float *Sf[kMaxDepth + 1], *HBf[kMaxDepth + 1];
+    // layered path: FP32 residual streams h, g, h', hbar; pre-activations a
+    // and the tangent terms S in BF16 (they are not accumulated)
+    float *Hf[kMaxDepth + 1], *Gf[kMaxDepth + 1], *HDf[kMaxDepth + 1], *HBf[kMaxDepth + 1];
+    bf16 *Af[kMaxDepth + 1], *Sf[kMaxDepth + 1];
     bf16 *Winx, *WinxT, *W[kMaxDepth + 1], *WT[kMaxDepth + 1], *Bx[kMaxDepth + 1], *BxT[kMaxDepth + 1];
     float* colpart;
     int* err;

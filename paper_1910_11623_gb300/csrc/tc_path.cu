@@ -133,8 +133,10 @@ fbsde_status bf16_create(fbsde_ctx* c) {
     auto add = [&](size_t n) { bytes += rup(n, 256); };
     add(2 * Pm * b->Dp * sizeof(bf16));
     for (int k = 0; k < 4; ++k) add(nl * b->OP_stride * sizeof(bf16));
-    if (layered_f32)
-        for (int k = 0; k < 6; ++k) add(nl * Pm * w * sizeof(float));
+    if (layered_f32) {
+        for (int k = 0; k < 4; ++k) add(nl * Pm * w * sizeof(float));
+        for (int k = 0; k < 2; ++k) add(nl * Pm * w * sizeof(bf16));
+    }
     add((size_t)w * b->Dp * 2); add((size_t)b->Dn * b->wp * 2);
     for (int l = 1; l <= L; ++l) {
         add((size_t)w * b->wp * 2); add((size_t)w * b->wp * 2);
@@ -165,16 +167,19 @@ fbsde_status bf16_create(fbsde_ctx* c) {
     b->Vb = (bf16*)take(Pm * b->Dp * sizeof(bf16));
     bf16* blk[4];
     for (int k = 0; k < 4; ++k) blk[k] = (bf16*)take(nl * b->OP_stride * sizeof(bf16));
-    float* fblk[6] = {};
-    if (layered_f32)
-        for (int k = 0; k < 6; ++k) fblk[k] = (float*)take(nl * Pm * w * sizeof(float));
+    float* fblk[4] = {};
+    bf16* hblk[2] = {};
+    if (layered_f32) {
+        for (int k = 0; k < 4; ++k) fblk[k] = (float*)take(nl * Pm * w * sizeof(float));
+        for (int k = 0; k < 2; ++k) hblk[k] = (bf16*)take(nl * Pm * w * sizeof(bf16));
+    }
     for (int l = 0; l <= L; ++l) {
         b->Hb[l] = blk[0] + l * b->OP_stride; b->Eb[l] = blk[1] + l * b->OP_stride;
         b->HDb[l] = blk[2] + l * b->OP_stride; b->ABb[l] = blk[3] + l * b->OP_stride;
         if (layered_f32) {
             const size_t o = (size_t)l * Pm * w;
-            b->Af[l] = fblk[0] + o; b->Hf[l] = fblk[1] + o; b->Gf[l] = fblk[2] + o;
-            b->HDf[l] = fblk[3] + o; b->Sf[l] = fblk[4] + o; b->HBf[l] = fblk[5] + o;
+            b->Hf[l] = fblk[0] + o; b->Gf[l] = fblk[1] + o; b->HDf[l] = fblk[2] + o; b->HBf[l] = fblk[3] + o;
+            b->Af[l] = hblk[0] + o; b->Sf[l] = hblk[1] + o;
         }
     }
     b->Winx = (bf16*)take((size_t)w * b->Dp * 2);
@@ -259,6 +264,21 @@ __device__ __forceinline__ void st16f(float* p, const float (&v)[16]) {
 #pragma unroll
     for (int i = 0; i < 4; ++i) q[i] = make_float4(v[4 * i], v[4 * i + 1], v[4 * i + 2], v[4 * i + 3]);
 }
+// Sixteen BF16 values (32-byte aligned) as floats.
+__device__ __forceinline__ void ld16b(const bf16* p, float (&v)[16]) {
+    const uint4* q = reinterpret_cast<const uint4*>(p);
+#pragma unroll
+    for (int i = 0; i < 2; ++i) {
+        const uint4 u = __ldg(q + i);
+        const uint32_t w4[4] = {u.x, u.y, u.z, u.w};
+#pragma unroll
+        for (int k = 0; k < 4; ++k) {
+            const float2 f = __bfloat1622float2(*reinterpret_cast<const __nv_bfloat162*>(&w4[k]));
+            v[8 * i + 2 * k] = f.x;
+            v[8 * i + 2 * k + 1] = f.y;
+        }
+    }
+}
 __device__ __forceinline__ void st16b(bf16* p, const float (&v)[16]) {
     uint4 u[2];
     uint32_t* w = reinterpret_cast<uint32_t*>(u);
@@ -276,7 +296,7 @@ __device__ __forceinline__ void st16b(bf16* p, const float (&v)[16]) {
 
 struct EpiFwdB {  // a = acc + b + t tcol; h = s hprev + c act(a)
     const float* bias; const float* tcol; int K0; const float* hprev; float s, c;
-    float* aout; float* hout; bf16* hbout; int w, wp, M; float dt; int act;
+    bf16* aout; float* hout; bf16* hbout; int w, wp, M; float dt; int act;
     __device__ void operator()(int row, int c0, const float (&v)[16], int) const {
         const float t = (float)(row / M) * dt;
         float a[16], h[16], hp[16];
@@ -288,19 +308,19 @@ struct EpiFwdB {  // a = acc + b + t tcol; h = s hprev + c act(a)
             const float f = act3_fast(act, a[j]).f;
             h[j] = (hprev ? s * hp[j] : 0.f) + c * f;
         }
-        st16f(aout + (size_t)row * w + c0, a);
+        st16b(aout + (size_t)row * w + c0, a);
         st16f(hout + (size_t)row * w + c0, h);
         st16b(hbout + (size_t)row * wp + c0, h);
     }
 };
 
 struct EpiRevB {  // g = s g_l + acc; e = c_prev act'(a_prev) g
-    const float* gl; float s; const float* aprev; float cprev;
+    const float* gl; float s; const bf16* aprev; float cprev;
     float* gout; bf16* eout; int w, wp; int act;
     __device__ void operator()(int row, int c0, const float (&v)[16], int) const {
         float g[16], e[16], gv[16], ap[16];
         ld16f(gl + (size_t)row * w + c0, gv);
-        ld16f(aprev + (size_t)row * w + c0, ap);
+        ld16b(aprev + (size_t)row * w + c0, ap);
 #pragma unroll
         for (int j = 0; j < 16; ++j) {
             g[j] = s * gv[j] + v[j];
@@ -322,12 +342,12 @@ struct EpiZB {  // Z (+)= acc, columns < D
 };
 
 struct EpiTanB {  // h' = s h'_prev + c act'(a) a'; S = c act''(a) a' g
-    const float* a; const float* hdprev; const float* g; float s, c;
-    float* hdout; bf16* hdbout; float* sout; int w, wp; int act;
+    const bf16* a; const float* hdprev; const float* g; float s, c;
+    float* hdout; bf16* hdbout; bf16* sout; int w, wp; int act;
     __device__ void operator()(int row, int c0, const float (&v)[16], int) const {
         float av[16], gv[16], hp[16], hd[16], sv[16];
         const size_t o = (size_t)row * w + c0;
-        ld16f(a + o, av);
+        ld16b(a + o, av);
         ld16f(g + o, gv);
         if (hdprev) ld16f(hdprev + o, hp);
 #pragma unroll
@@ -338,19 +358,19 @@ struct EpiTanB {  // h' = s h'_prev + c act'(a) a'; S = c act''(a) a' g
         }
         st16f(hdout + o, hd);
         st16b(hdbout + (size_t)row * wp + c0, hd);
-        st16f(sout + o, sv);
+        st16b(sout + o, sv);
     }
 };
 
 struct EpiAdjB {  // hbar = s hbar_l + acc; abar_prev = c_prev act'(a_prev) hbar + S_prev
-    const float* hbl; float s; const float* aprev; const float* sprev; float cprev;
+    const float* hbl; float s; const bf16* aprev; const bf16* sprev; float cprev;
     float* hbout; bf16* about; int w, wp; int act;
     __device__ void operator()(int row, int c0, const float (&v)[16], int) const {
         float hv[16], ap[16], sp[16], hb[16], ab[16];
         const size_t o = (size_t)row * w + c0;
         ld16f(hbl + o, hv);
-        ld16f(aprev + o, ap);
-        ld16f(sprev + o, sp);
+        ld16b(aprev + o, ap);
+        ld16b(sprev + o, sp);
 #pragma unroll
         for (int j = 0; j < 16; ++j) {
             hb[j] = s * hv[j] + v[j];
@@ -419,19 +439,19 @@ __global__ void k_cvt_bf16_batch(const __grid_constant__ CvtBatch b) {
 }
 
 // g_L = w_o, e_L = c_L act'(a_L) w_o (BF16)
-__global__ void k_top_rev_b(size_t P, int w, int wp, const float* __restrict__ aL, const float* __restrict__ wo,
+__global__ void k_top_rev_b(size_t P, int w, int wp, const bf16* __restrict__ aL, const float* __restrict__ wo,
                             float cL, int act, float* __restrict__ gL, bf16* __restrict__ eL) {
     const size_t i = (size_t)blockIdx.x * blockDim.x + threadIdx.x;
     if (i >= P * w) return;
     const size_t p = i / w;
     const int j = (int)(i % w);
     gL[i] = wo[j];
-    eL[p * wp + j] = __float2bfloat16_rn(cL * act3_fast(act, aL[i]).d1 * wo[j]);
+    eL[p * wp + j] = __float2bfloat16_rn(cL * act3_fast(act, __bfloat162float(aL[i])).d1 * wo[j]);
 }
 
 // hbar_L = alpha w_o, abar_L = c_L act'(a_L) hbar_L + S_L (BF16)
-__global__ void k_top_adj_b(size_t P, int w, int wp, const float* __restrict__ aL, const float* __restrict__ wo,
-                            const float* __restrict__ alpha, const float* __restrict__ SL, float cL, int act,
+__global__ void k_top_adj_b(size_t P, int w, int wp, const bf16* __restrict__ aL, const float* __restrict__ wo,
+                            const float* __restrict__ alpha, const bf16* __restrict__ SL, float cL, int act,
                             float* __restrict__ hbL, bf16* __restrict__ abL) {
     const size_t i = (size_t)blockIdx.x * blockDim.x + threadIdx.x;
     if (i >= P * w) return;
@@ -439,7 +459,8 @@ __global__ void k_top_adj_b(size_t P, int w, int wp, const float* __restrict__ a
     const int j = (int)(i % w);
     const float hb = alpha[p] * wo[j];
     hbL[i] = hb;
-    abL[p * wp + j] = __float2bfloat16_rn(cL * act3_fast(act, aL[i]).d1 * hb + SL[i]);
+    abL[p * wp + j] = __float2bfloat16_rn(cL * act3_fast(act, __bfloat162float(aL[i])).d1 * hb +
+                                          __bfloat162float(SL[i]));
 }
 
 // Partial column sums over a range of points, fixed order:
