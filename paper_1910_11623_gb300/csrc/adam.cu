@@ -11,11 +11,14 @@ namespace fbsde {
 // The bias corrections 1 / (1 - beta^step) are formed on the device (FP64,
 // once per block) from the step passed by value or read from step_dev, so a
 // step replayed from a CUDA graph computes exactly what a direct call does.
+// The weights 1 - beta of the new gradient are formed in FP64 before rounding
+// (1 - (float)0.999 would be 1.3e-5 away from 1e-3).
 __global__ void k_adam(size_t n, float* __restrict__ theta, const float* __restrict__ g,
                        float* __restrict__ m, float* __restrict__ v, float lr, double b1d, double b2d,
                        uint64_t step_host, const uint64_t* __restrict__ step_dev, float eps) {
     __shared__ float inv_bc[2];
     const float b1 = (float)b1d, b2 = (float)b2d;
+    const float c1 = (float)(1.0 - b1d), c2 = (float)(1.0 - b2d);
     if (threadIdx.x == 0) {
         const double step = (double)(step_dev ? *step_dev : step_host);
         inv_bc[0] = (float)(1.0 / (1.0 - pow(b1d, step)));
@@ -26,8 +29,8 @@ __global__ void k_adam(size_t n, float* __restrict__ theta, const float* __restr
     size_t i = (size_t)blockIdx.x * blockDim.x + threadIdx.x;
     if (i >= n) return;
     const float gi = g[i];
-    const float mi = b1 * m[i] + (1.f - b1) * gi;
-    const float vi = b2 * v[i] + (1.f - b2) * gi * gi;
+    const float mi = b1 * m[i] + c1 * gi;
+    const float vi = b2 * v[i] + c2 * gi * gi;
     m[i] = mi;
     v[i] = vi;
     theta[i] -= lr * (mi * inv_bc1) / (sqrtf(vi * inv_bc2) + eps);
