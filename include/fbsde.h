@@ -325,6 +325,20 @@ fbsde_status fbsde_set_x0(fbsde_ctx* ctx, const double* x0_host);
  * flags are cleared by the call. */
 fbsde_status fbsde_check_finite(fbsde_ctx* ctx);
 
+/* Test hook for the bounded waits of the tensor-core kernels (not a
+ * computation of the paper).  The next launch of the context's pipelined
+ * forward kernel and of its pipelined backward kernel (FC and ResNet networks
+ * in BF16) each start with a wait on a barrier that nothing completes, with a
+ * wait budget of about 10 us: every role of the kernel gives up there, before
+ * it issues any copy or contraction, sets the context's device error flag and
+ * releases its TMEM, so the launches complete and the context stays usable.
+ * The next fbsde_check_finite then returns FBSDE_ERR_TIMEOUT (and clears the
+ * flag); the results of those launches are invalid.  The hook disarms itself
+ * at the launch it affects.  FBSDE_ERR_UNSUPPORTED for a context whose
+ * network is not served by the pipelined kernels (NAIS-Net, FP8, FP32, the
+ * layered path). */
+fbsde_status fbsde_test_timeout_once(fbsde_ctx* ctx);
+
 /* Replace x0 from a device buffer (D floats), ordered on the context stream:
  * the variant of fbsde_set_x0 for callers that stage x0 in device memory. */
 fbsde_status fbsde_set_x0_device(fbsde_ctx* ctx, const float* x0_dev);

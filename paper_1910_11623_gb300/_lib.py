@@ -73,6 +73,7 @@ SIGNATURES = {
                                      c_uint64, c_float, c_void_p, c_void_p]),
     "fbsde_set_x0": (c_int, [c_void_p, POINTER(c_double)]),
     "fbsde_check_finite": (c_int, [c_void_p]),
+    "fbsde_test_timeout_once": (c_int, [c_void_p]),
     "fbsde_set_x0_device": (c_int, [c_void_p, c_void_p]),
     "fbsde_profile_enable": (c_int, [c_void_p, c_int]),
     "fbsde_profile_read": (c_int, [c_void_p, c_int, POINTER(c_double), POINTER(c_uint64),
@@ -303,6 +304,10 @@ def fbsde_set_x0(ctx, x0):
 
 def fbsde_check_finite(ctx):
     check(load().fbsde_check_finite(ctx), "fbsde_check_finite", ctx)
+
+
+def fbsde_test_timeout_once(ctx):
+    check(load().fbsde_test_timeout_once(ctx), "fbsde_test_timeout_once", ctx)
 
 
 def fbsde_set_x0_device(ctx, x0_ptr: int):

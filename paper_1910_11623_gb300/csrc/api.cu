@@ -478,6 +478,11 @@ fbsde_status fbsde_profile_read(fbsde_ctx* ctx, int cls, double* ms_total, uint6
 
 uint64_t fbsde_launch_count(const fbsde_ctx* ctx) { return ctx ? ctx->n_launch : 0; }
 
+fbsde_status fbsde_test_timeout_once(fbsde_ctx* ctx) {
+    if (!ctx) return FBSDE_ERR_INVALID;
+    return arm_timeout_test(ctx);
+}
+
 fbsde_status fbsde_check_finite(fbsde_ctx* ctx) {
     if (!ctx) return FBSDE_ERR_INVALID;
     int flag = 0, timeout = 0;

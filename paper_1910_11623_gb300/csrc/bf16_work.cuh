@@ -88,6 +88,9 @@ struct Bf16Work {
     uint8_t* W8[kMaxDepth + 1] = {};
     CUtensorMap mW8[kMaxDepth + 1];
     float* f8inv = nullptr;  // [L + 1]: 1 / (scale of h_{l-1} x scale of W_l)
+    // Test hook (fbsde_test_timeout_once): the next launch of each fused kernel
+    // gives up at its first wait, before it issues any copy or contraction.
+    int gate_fwd = 0, gate_bwd = 0;
 };
 
 // Scale of the E4M3 copy of h_l (the operand of layer l + 1): the largest

@@ -181,6 +181,8 @@ fbsde_status nais_project(fbsde_ctx* ctx, float* theta);
 fbsde_status bf16_create(fbsde_ctx* ctx);
 // Device flag the tensor-core kernels raise when a bounded wait runs out (NULL: no BF16 workspace).
 int* bf16_error_flag(fbsde_ctx* ctx);
+// Arms the test hook of the pipelined kernels (fbsde_test_timeout_once).
+fbsde_status arm_timeout_test(fbsde_ctx* c);
 void bf16_destroy(fbsde_ctx* ctx);
 fbsde_status bf16_prepare_weights(fbsde_ctx* ctx, const float* theta);
 fbsde_status bf16_forward(fbsde_ctx* ctx, const float* theta, bool for_grad);

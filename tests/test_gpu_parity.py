@@ -338,6 +338,37 @@ def test_nonfinite_is_reported(P):
     s.close()
 
 
+def test_bounded_wait_gives_up_and_is_reported(P):
+    # The pipelined kernels' waits are bounded.  The test hook makes the next
+    # forward and backward launch wait first on a barrier that nothing
+    # completes (about 10 us budget): every role gives up before it issues a
+    # copy or a contraction, the launch completes, and fbsde_check_finite
+    # reports FBSDE_ERR_TIMEOUT.  The context then computes correctly again.
+    from paper_1910_11623_gb300 import _lib as L
+    prob = P.ProblemSpec(kind="bsb", D=6, N=4, M=40, x0=[1.0, 0.5] * 3)
+    arch = P.ArchSpec(kind="resnet", width=32, depth=2, act="tanh", prec="bf16")
+    s = _solver(P, prob, arch, seed=3)
+    th64, th = _theta_pair(P, s, prob, arch, 3, 0.1)
+    L.fbsde_test_timeout_once(s.ctx)
+    s.rollout_grad(th, 5)
+    with pytest.raises(L.FBSDEError) as ei:
+        s.check_finite()
+    assert ei.value.status == L.FBSDE_ERR_TIMEOUT
+    s.check_finite()  # reported once, then cleared
+    op, oa = oracle_specs(prob, arch)
+    ro, g = F.rollout_grad(op, oa, th64, 3, 5)
+    loss, y0, grad = s.rollout_grad(th, 5)
+    s.check_finite()
+    assert rel(loss.item(), ro.loss) < TOL["bf16"] and rel_max(grad.cpu().numpy(), g) < TOL["bf16"]
+    # contexts the pipelined kernels do not serve refuse the hook
+    s2 = _solver(P, prob, P.ArchSpec(kind="nais", width=32, depth=2, act="tanh", prec="bf16"), seed=3)
+    with pytest.raises(L.FBSDEError) as ei:
+        L.fbsde_test_timeout_once(s2.ctx)
+    assert ei.value.status == L.FBSDE_ERR_UNSUPPORTED
+    s2.close()
+    s.close()
+
+
 @pytest.mark.parametrize("prec", ["fp32", "bf16"])
 def test_multilevel_schedule(P, prec):
     # Section 3.2: levels 2 -> 4 -> 8 with Theta and the Adam moments carried
