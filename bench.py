@@ -45,7 +45,20 @@ def parse_args():
     ap.add_argument("--fp32-steps", type=int, default=10,
                     help="timed steps of the FP32 form beside a BF16 run (0: skip)")
     ap.add_argument("--accuracy-steps", type=int, default=5000,
-                    help="Adam steps of the accuracy run (0: skip)")
+                    help="Adam steps of each BF16 accuracy run (0: skip)")
+    ap.add_argument("--accuracy-seeds", type=int, default=3,
+                    help="seeds of the accuracy runs (each form)")
+    ap.add_argument("--fp32-accuracy-steps", type=int, default=3000,
+                    help="at most this many steps of each FP32-form accuracy run under the decayed learning "
+                         "rate (it stops once the 1%% band is held; 0: skip)")
+    ap.add_argument("--fp32-accuracy-seeds", type=int, default=1,
+                    help="seeds of the FP32-form accuracy runs")
+    ap.add_argument("--lr-decay-step", type=int, default=2000,
+                    help="accuracy runs with the learning rate multiplied by --lr-decay-factor after this step "
+                         "(beside the paper's constant rate; 0: skip)")
+    ap.add_argument("--lr-decay-factor", type=float, default=0.1)
+    ap.add_argument("--decay-accuracy-steps", type=int, default=3000,
+                    help="steps of each BF16 run with the decayed learning rate")
     ap.add_argument("--cpu-iters", type=int, default=1,
                     help="whole-workload FP64 oracle steps timed for the CPU baseline")
     ap.add_argument("--no-cpu-baseline", action="store_true")
@@ -323,11 +336,131 @@ def batched_run(P, steps: int, lr: float):
     return res
 
 
-def multilevel_run(P, w, target, max_steps):
+CHECK_EVERY = 50   # steps between Y0 checks
+HOLD_CHECKS = 10   # consecutive checks within 1% that count as having reached it
+TAIL_STEPS = 250   # Y0 averaged over the last steps of a run
+
+
+class Held:
+    """Tracks |Y0 - target| / target <= tol at the checks: the first check
+    inside, and the first check of a run of `hold` consecutive checks inside
+    (the step and wall time at which Y0 entered the band it then stayed in)."""
+
+    def __init__(self, target, tol=0.01, hold=HOLD_CHECKS):
+        self.target, self.tol, self.hold = target, tol, hold
+        self.first = None     # (step, wall_s)
+        self.entry = None     # candidate start of a run inside the band
+        self.run = 0
+        self.held = None      # (step, wall_s) of the start of the first held run
+        self.checks = []      # (step, rel_err)
+
+    def check(self, step, wall, y0):
+        err = abs(y0 - self.target) / self.target
+        self.checks.append((step, err))
+        if err <= self.tol:
+            if self.first is None:
+                self.first = (step, wall)
+            if self.run == 0:
+                self.entry = (step, wall)
+            self.run += 1
+            if self.held is None and self.run >= self.hold:
+                self.held = self.entry
+        else:
+            self.run = 0
+        return self.held is not None
+
+
+def accuracy_run(P, w, target, seed, max_steps, stop_when_held=False, keep=False, decay=None):
+    """Train from Theta_0 of `seed` on the workload's grid in schedule calls
+    of CHECK_EVERY steps (one Y0 read-back per call), checking |Y0 - target|
+    after each call.  Reports the first check within 1%, the start of the
+    first run of HOLD_CHECKS consecutive checks within 1% (steps and wall
+    time), the share of later checks still within 1%, and Y0 averaged over
+    the last TAIL_STEPS steps.  With stop_when_held, training ends once the
+    held run is established.  With keep, also returns the solver and the
+    trained Theta (the caller closes the solver).  decay = (step, factor):
+    the learning rate is multiplied by factor after that step (not in the
+    paper, which trains at a constant 1e-3)."""
+    import numpy as np
+    import torch
+    N = w.problem.N
+    s = P.Solver(w.problem, w.arch, seed=seed)
+    th = s.init_params()
+    m, v = torch.zeros_like(th), torch.zeros_like(th)
+    torch.cuda.synchronize()
+    hd = Held(target)
+    trace = []
+    t0 = time.perf_counter()
+    step = 1
+    while step <= max_steps:
+        k = min(CHECK_EVERY, max_steps - step + 1)
+        lr = w.lr
+        if decay and step > decay[0]:
+            lr = w.lr * decay[1]
+        elif decay:
+            k = min(k, decay[0] - step + 1)
+        _, y0 = s.train_schedule(th, m, v, [N], [k], step, lr)
+        y0 = y0.cpu().numpy().astype(np.float64)
+        trace.extend(y0.tolist())
+        step += k
+        if hd.check(step - 1, time.perf_counter() - t0, float(y0[-1])) and stop_when_held:
+            break
+    wall = time.perf_counter() - t0
+    if not keep:
+        s.close()
+    tail = float(np.mean(trace[-TAIL_STEPS:]))
+    after = [e for st, e in hd.checks if hd.held and st >= hd.held[0]]
+    res = {"seed": seed, "steps": len(trace), "wall_s": wall,
+            "first_within_1pct": {"step": hd.first[0], "s": hd.first[1]} if hd.first else None,
+            "held_within_1pct": {"step": hd.held[0], "s": hd.held[1]} if hd.held else None,
+            "share_of_checks_within_1pct_after_held": (sum(e <= 0.01 for e in after) / len(after)) if after else None,
+            "y0_last": trace[-1], "y0_tail_mean": tail, "y0_tail_rel_err": abs(tail - target) / target,
+            "max_rel_err_last_1000_steps": float(np.max(np.abs(np.array(trace[-1000:]) - target)) / target)}
+    return (res, s, th) if keep else res
+
+
+def accuracy_study(P, w, target, seeds, bf16_steps, fp32_steps, decay=None, fp32_seeds=None, keep_first=True):
+    """accuracy_run for `seeds` seeds in both forms: the BF16 form for
+    bf16_steps steps, the FP32 form until its held run is established (at
+    most fp32_steps).  The speed-up at that accuracy is the ratio of the
+    median times to the held 1% band.  Returns the summary and (solver,
+    Theta) of the BF16 run of the workload's own seed (to be closed by the
+    caller)."""
+    import statistics as st
+    trained = None
+    out = {"criterion": f"|Y0 - {target:.6f}| / {target:.6f} <= 1% at {HOLD_CHECKS} consecutive checks "
+                        f"{CHECK_EVERY} steps apart; time and step of the first check of that run",
+           "tail_mean_over_steps": TAIL_STEPS}
+    if decay:
+        out["lr_schedule"] = f"{w.lr:g} for steps 1..{decay[0]}, then {w.lr * decay[1]:g}"
+    for form, steps, stop in (("bf16", bf16_steps, False), ("fp32", fp32_steps, True)):
+        if steps <= 0:
+            continue
+        wf = w.with_prec(form)
+        runs = []
+        for k in range(seeds if form == "bf16" or fp32_seeds is None else fp32_seeds):
+            if form == "bf16" and k == 0 and keep_first:
+                r, s0, th0 = accuracy_run(P, wf, target, w.seed, steps, stop, keep=True, decay=decay)
+                trained = (s0, th0)
+            else:
+                r = accuracy_run(P, wf, target, w.seed + k, steps, stop, decay=decay)
+            runs.append(r)
+        held = [r["held_within_1pct"]["s"] for r in runs if r["held_within_1pct"]]
+        out[form] = {"runs": runs, "seeds_held": len(held),
+                     "median_time_to_held_1pct_s": st.median(held) if len(held) == len(runs) else None}
+    b, f = out.get("bf16", {}), out.get("fp32", {})
+    if b.get("median_time_to_held_1pct_s") and f.get("median_time_to_held_1pct_s"):
+        out["speedup_bf16_vs_fp32_to_held_1pct"] = f["median_time_to_held_1pct_s"] / b["median_time_to_held_1pct_s"]
+    return out, trained
+
+
+def multilevel_run(P, w, target, max_steps, decay=None):
     """Multilevel training (Section 3.2) from the same Theta_0 as the
     single-level accuracy run: fixed Adam steps on the coarse grids, then the
-    target grid until |Y0 - closed form| <= 1% (checked every 50 steps, as in
-    the single-level run).  Wall time includes every level."""
+    target grid until |Y0 - closed form| stays within 1% (Held, as in the
+    single-level runs).  Wall time includes every level.  decay = (step,
+    factor): the learning rate is multiplied by factor after that (global)
+    step, as in the single-level runs with decay."""
     import torch
     levels = list(P.workloads.MULTILEVEL_LEVELS)
     N = w.problem.N
@@ -336,33 +469,42 @@ def multilevel_run(P, w, target, max_steps):
     m, v = torch.zeros_like(th), torch.zeros_like(th)
     torch.cuda.synchronize()
     t0 = time.perf_counter()
-    step, hit, per_level = 1, None, []
+    step, per_level = 1, []
+    hd = Held(target)
     for lv in levels:
         budget = P.workloads.MULTILEVEL_COARSE_STEPS if lv < N else max_steps
         done = 0
         tl = time.perf_counter()
         while done < budget:
-            k = min(50, budget - done)
-            _, y0 = s.train_schedule(th, m, v, [lv], [k], step, w.lr)
+            k = min(CHECK_EVERY, budget - done)
+            lr = w.lr
+            if decay and step > decay[0]:
+                lr = w.lr * decay[1]
+            elif decay:
+                k = min(k, decay[0] - step + 1)
+            _, y0 = s.train_schedule(th, m, v, [lv], [k], step, lr)
             step += k
             done += k
             err = abs(y0[-1].item() - target) / target
-            if lv == N and err <= 0.01:
-                hit = (time.perf_counter() - t0, step - 1)
+            if lv == N and hd.check(step - 1, time.perf_counter() - t0, y0[-1].item()):
                 break
         per_level.append({"N": lv, "steps": done, "wall_s": time.perf_counter() - tl, "y0_rel_err": err})
-        if hit:
+        if hd.held:
             break
     res = {"levels": levels, "coarse_steps_per_level": P.workloads.MULTILEVEL_COARSE_STEPS,
-           "per_level": per_level, "time_to_1pct_s": hit[0] if hit else None,
-           "steps_to_1pct": hit[1] if hit else None, "wall_s": time.perf_counter() - t0}
+           "per_level": per_level,
+           "criterion": f"{HOLD_CHECKS} consecutive checks within 1% on the N = {N} grid (time of the first)",
+           "time_to_held_1pct_s": hd.held[1] if hd.held else None,
+           "steps_to_held_1pct": hd.held[0] if hd.held else None,
+           "time_to_first_1pct_s": hd.first[1] if hd.first else None, "wall_s": time.perf_counter() - t0}
     s.close()
     return res
 
 
 def single_level_run(P, w, target, max_steps):
     """Training on the target grid alone from Theta_0 until |Y0 - closed form|
-    <= 1% (checked every 50 steps), in schedule calls of 50 steps."""
+    stays within 1% (Held: checked every CHECK_EVERY steps), in schedule
+    calls of CHECK_EVERY steps."""
     import torch
     N = w.problem.N
     s = P.Solver(w.problem, w.arch, seed=w.seed)
@@ -370,16 +512,19 @@ def single_level_run(P, w, target, max_steps):
     m, v = torch.zeros_like(th), torch.zeros_like(th)
     torch.cuda.synchronize()
     t0 = time.perf_counter()
-    step, hit, err = 1, None, None
+    step, err = 1, None
+    hd = Held(target)
     while step <= max_steps:
-        k = min(50, max_steps - step + 1)
+        k = min(CHECK_EVERY, max_steps - step + 1)
         _, y0 = s.train_schedule(th, m, v, [N], [k], step, w.lr)
         step += k
         err = abs(y0[-1].item() - target) / target
-        if err <= 0.01:
-            hit = (time.perf_counter() - t0, step - 1)
+        if hd.check(step - 1, time.perf_counter() - t0, y0[-1].item()):
             break
-    res = {"N": N, "time_to_1pct_s": hit[0] if hit else None, "steps_to_1pct": hit[1] if hit else None,
+    res = {"N": N, "criterion": f"{HOLD_CHECKS} consecutive checks within 1% (time of the first)",
+           "time_to_held_1pct_s": hd.held[1] if hd.held else None,
+           "steps_to_held_1pct": hd.held[0] if hd.held else None,
+           "time_to_first_1pct_s": hd.first[1] if hd.first else None,
            "y0_rel_err": err, "wall_s": time.perf_counter() - t0}
     s.close()
     return res
@@ -629,27 +774,19 @@ def main():
                 out["fp8_hidden_form"] = {"error": f"{type(exc).__name__}: {exc}"}
         torch.cuda.empty_cache()
 
-    # accuracy: train from Theta_0 and track |Y0 - closed form| / closed form
+    # accuracy: train from Theta_0 and track |Y0 - closed form| / closed form,
+    # several seeds, both forms
     if args.accuracy_steps > 0 and out is not None and w.problem.kind == "bsb" and w.problem.D == 100:
         target = P.workloads.BSB_Y0_D100
-        sa = P.Solver(w.problem, w.arch, seed=w.seed)
-        th = sa.init_params()
-        ma, va = torch.zeros_like(th), torch.zeros_like(th)
-        t0 = time.perf_counter()
-        t_hit, errs = None, []
-        for s in range(1, args.accuracy_steps + 1):
-            _, y0 = sa.train_step(th, ma, va, s, w.lr)
-            if s % 50 == 0 or s == args.accuracy_steps:
-                err = abs(y0.item() - target) / target
-                errs.append(err)
-                if t_hit is None and err <= 0.01:
-                    t_hit = (time.perf_counter() - t0, s)
-        _, y0 = sa.rollout_loss(th, 10**6)
-        out["accuracy"] = {"steps": args.accuracy_steps, "y0": y0.item(), "y0_closed_form": target,
-                           "y0_rel_err": abs(y0.item() - target) / target,
-                           "time_to_1pct_s": t_hit[0] if t_hit else None,
-                           "steps_to_1pct": t_hit[1] if t_hit else None,
-                           "wall_s": time.perf_counter() - t0}
+        # the paper's constant learning rate, BF16 form (the FP32 form is
+        # compared under the decayed schedule below, where the band can hold)
+        out["accuracy"], (sa, th) = accuracy_study(P, w, target, args.accuracy_seeds, args.accuracy_steps, 0)
+        if args.lr_decay_step > 0:
+            out["accuracy_lr_decay"], _ = accuracy_study(
+                P, w, target, args.accuracy_seeds, args.decay_accuracy_steps, args.fp32_accuracy_steps,
+                decay=(args.lr_decay_step, args.lr_decay_factor), fp32_seeds=args.fp32_accuracy_seeds,
+                keep_first=False)
+        # the trained Theta of the workload's own seed, for the generalisation check
         # generalisation (Section 4.2): the trained Theta at perturbed x0
         x0 = list(w.problem.x0)
         rng = __import__("random").Random(w.seed)
@@ -660,8 +797,12 @@ def main():
             name: {"y0": g, "closed_form": P.workloads.bsb_y0(xc),
                    "rel_err": abs(g - P.workloads.bsb_y0(xc)) / P.workloads.bsb_y0(xc)}
             for (name, xc), g in zip(cases.items(), got)}
+        sa.close()
         del sa
-        out["multilevel"] = multilevel_run(P, w, target, args.accuracy_steps)
+        decay = (args.lr_decay_step, args.lr_decay_factor) if args.lr_decay_step > 0 else None
+        out["multilevel"] = multilevel_run(P, w, target, args.accuracy_steps, decay)
+        if decay:
+            out["multilevel"]["lr_schedule"] = out["accuracy_lr_decay"]["lr_schedule"]
 
     # the stable network of the paper (NAIS-Net, HJB, Section 4): BF16 form
     # (fused per-tile kernels) and FP32 form
