@@ -152,15 +152,16 @@ def measured_peaks():
             "sm_max_mhz": 2070.0}, "fallback"
 
 
-# Sources of the fused point-contraction kernels: a committed DRAM-traffic
-# figure is reported only while these are unchanged since its capture.
-KERNEL_SOURCES = ("fused.cu", "tc_common.cuh", "bf16_work.cuh")
+# Sources of the fused point-contraction kernels (FC / ResNet: the pipelined
+# kernels): a committed DRAM-traffic figure is reported only while the
+# sources it names are unchanged since its capture.
+KERNEL_SOURCES = ("fused_pipe.cu", "fused_common.cuh", "tc_common.cuh", "bf16_work.cuh")
 
 
-def source_hash() -> str:
+def source_hash(files=KERNEL_SOURCES) -> str:
     h = hashlib.sha256()
     csrc = os.path.join(ROOT, "paper_1910_11623_gb300", "csrc")
-    for f in KERNEL_SOURCES:
+    for f in files:
         with open(os.path.join(csrc, f), "rb") as fh:
             h.update(f.encode() + fh.read())
     return h.hexdigest()[:16]
@@ -174,7 +175,7 @@ def ncu_traffic(form: str, workload: str):
         return None
     with open(path) as f:
         d = json.load(f)
-    if d.get("source_hash") != source_hash():
+    if d.get("source_hash") != source_hash(tuple(d.get("hash_of", KERNEL_SOURCES))):
         return None
     return d.get("dram_bytes_per_launch")
 
