@@ -49,7 +49,7 @@ namespace fbsde {
 
 constexpr int kPGroups = 4;                      // epilogue warpgroups
 constexpr int kPThreads = 128 * (1 + kPGroups);  // warpgroup 0: producer, MMA, store warp, spare
-constexpr int kPStages = 4;                      // weight ring stages of the forward kernel (32 KB each)
+constexpr int kPStages = 3;                      // weight ring stages of the forward kernel (32 KB each)
 constexpr int kPBwdStages = 2;                   // the backward kernel's two operand tiles leave room for two
 // 20 warps: 5 per SM sub-partition, 96 registers per thread at launch;
 // warpgroup 0 then drops to kPRegsCtl and the epilogue warpgroups rise to
@@ -138,6 +138,12 @@ __device__ __forceinline__ void slab_release(uint64_t* bar, int lane) {
     if (lane == 0) tc::mbar_arrive(bar);
 }
 // Sixteen consecutive floats from a 16-byte-aligned shared-memory address.
+// 8 floats of a read-only table in global memory (L1-cached)
+__device__ __forceinline__ void ld_f8g(const float* src, float* v) {
+    const float4 a = __ldg(reinterpret_cast<const float4*>(src)), b = __ldg(reinterpret_cast<const float4*>(src) + 1);
+    v[0] = a.x; v[1] = a.y; v[2] = a.z; v[3] = a.w;
+    v[4] = b.x; v[5] = b.y; v[6] = b.z; v[7] = b.w;
+}
 __device__ __forceinline__ void ld_f16v(const float* src, float (&v)[16]) {
 #pragma unroll
     for (int k = 0; k < 4; ++k) {
@@ -165,8 +171,9 @@ __device__ __forceinline__ void st_g8h(uint32_t* blk, int row, int c0, const uin
                  "r"(u[2]), "r"(u[3]), "l"(pol) : "memory");
 }
 __device__ __forceinline__ void ld_g16(const uint32_t* blk, int row, int c0, uint32_t (&u)[8]) {
+    // through L2 only: L1 keeps the register spills and the parameter table
     const uint4* q = reinterpret_cast<const uint4*>(blk + ((size_t)(c0 >> 4) * 128 + row) * 8);
-    const uint4 a = q[0], b = q[1];
+    const uint4 a = __ldcg(q), b = __ldcg(q + 1);
     u[0] = a.x; u[1] = a.y; u[2] = a.z; u[3] = a.w;
     u[4] = b.x; u[5] = b.y; u[6] = b.z; u[7] = b.w;
 }
@@ -599,10 +606,12 @@ __device__ __forceinline__ void bwdp_body(const BwdArgs& a, const int cta, const
     uint8_t* tile_h = smem;                  // h_l in the up-sweep, abar_l in the adjoint sweep
     uint8_t* tile_d = smem + kFTileBytes;    // h'_l
     uint8_t* ring = smem + 2 * kFTileBytes;
-    float* ptab = (float*)(ring + kPBwdStages * kFStageBytes);
+    // the per-column parameters are read from the table in global memory (held
+    // in L1): without a copy in shared memory the kernel fits the 196 KB
+    // shared-memory configuration, which leaves 60 KB of L1
+    const float* ptab = a.pvec;
     const int L = a.L;
-    const int prows = param_rows(L, 0);
-    PipeBars* B = (PipeBars*)(((uintptr_t)(ptab + prows * a.w) + 15) & ~(uintptr_t)15);
+    PipeBars* B = (PipeBars*)(ring + kPBwdStages * kFStageBytes);
     volatile int* abort_flag = &B->abort_flag;
 
     const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
@@ -611,8 +620,6 @@ __device__ __forceinline__ void bwdp_body(const BwdArgs& a, const int cta, const
     const int nkw = a.wp / 64, nkx = a.Dp / 64;
     const long long budget = a.wait_budget;
 
-    for (int k = threadIdx.x; k < prows * a.w / 4; k += blockDim.x)
-        reinterpret_cast<float4*>(ptab)[k] = __ldg(reinterpret_cast<const float4*>(a.pvec) + k);
     if (threadIdx.x == 0) {
         for (int s = 0; s < kPBwdStages; ++s) {
             tc::mbar_init(&B->bfull[s], 1);
@@ -813,14 +820,14 @@ __device__ __forceinline__ void bwdp_body(const BwdArgs& a, const int cta, const
                     tc::tmem_wait_ld();
                     if (c0 < a.w) {
                         float bv[8], g[8], hp[8], hdp[8];
-                        ld_f8(bias + cc, bv);
+                        ld_f8g(bias + cc, bv);
                         if (LIFT) {
                             float tw[8];
-                            ld_f8(win0 + cc, tw);
+                            ld_f8g(win0 + cc, tw);
 #pragma unroll
                             for (int j = 0; j < 8; ++j) bv[j] = fmaf(tval, tw[j], bv[j]);
                         }
-                        if (top) ld_f8(wo + cc, g);
+                        if (top) ld_f8g(wo + cc, g);
                         else {
 #pragma unroll
                             for (int k = 0; k < 4; ++k) {
@@ -973,6 +980,11 @@ template <class K>
 static cudaError_t prepare_pipe(K kernel, size_t smem) {
     cudaError_t e = cudaFuncSetAttribute(kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
     if (e != cudaSuccess) return e;
+    // the smallest shared-memory configuration that holds the block (196 of 228
+    // KB when it fits): the rest of the SM's 256 KB is L1, which keeps the
+    // epilogue's register spills close
+    e = cudaFuncSetAttribute(kernel, cudaFuncAttributePreferredSharedMemoryCarveout, 85);
+    if (e != cudaSuccess) return e;
     // the register split assumes exactly kPRegsLaunch registers per thread at launch
     cudaFuncAttributes fa;
     e = cudaFuncGetAttributes(&fa, kernel);
@@ -1002,8 +1014,9 @@ cudaError_t launch_fwd_pipe(const FwdZArgs& a, int act_tanh, int res, int grid, 
 }
 
 size_t bwd_pipe_smem_bytes(int L, int w) {
-    return 1024 + 2 * kFTileBytes + (size_t)kPBwdStages * kFStageBytes + (size_t)param_rows(L, 0) * w * 4 + 16 +
-           sizeof(PipeBars);
+    (void)L;
+    (void)w;
+    return 1024 + 2 * kFTileBytes + (size_t)kPBwdStages * kFStageBytes + sizeof(PipeBars);
 }
 
 cudaError_t launch_bwd_pipe(const BwdArgs& a, int act_tanh, int res, int grid, cudaStream_t st) {
