@@ -91,6 +91,9 @@ struct Bf16Work {
     // Test hook (fbsde_test_timeout_once): the next launch of each fused kernel
     // gives up at its first wait, before it issues any copy or contraction.
     int gate_fwd = 0, gate_bwd = 0;
+    // pipelined backward: per tile and 32-row group, the column sums of
+    // alpha h_L + h'_L (the read-out gradient), summed in order afterwards
+    float* wopart = nullptr;
 };
 
 // Scale of the E4M3 copy of h_l (the operand of layer l + 1): the largest

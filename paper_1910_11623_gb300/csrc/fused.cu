@@ -978,6 +978,7 @@ static void bwd_args(fbsde_ctx* c, const float* theta, BwdArgs& a) {
     a.X = c->X; a.V = c->V; a.alpha = c->alpha; a.theta = theta;
     a.G = (const uint32_t*)b->G; a.G_words = b->G_stride / 2;
     a.HbL = b->Hb[c->L];
+    a.wopart = b->wopart;
     a.scratch = (uint32_t*)b->scratch;
     a.off = param_offsets(c);
     a.P = (int)c->P(); a.M = c->M; a.D = c->D; a.Dp = b->Dp; a.w = c->w; a.wp = b->wp;

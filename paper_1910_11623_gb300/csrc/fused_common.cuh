@@ -375,7 +375,8 @@ struct BwdArgs {
     const float* theta;
     const uint32_t* G;         // g_l, l < L, column-pair-major per tile (from k_fused_fwdz)
     unsigned long long G_words;
-    bf16* HbL;                 // h_L rows of wp (its tile slot holds abar_L)
+    bf16* HbL;                 // h_L rows of wp (its tile slot holds abar_L); general kernels
+    float* wopart;             // pipelined kernels: [ntiles][4][w] partial sums of alpha h_L + h'_L
     uint32_t* scratch;         // per CTA: act'(a_l) and S_l, l < L, column-pair-major
     ParamOffsets off;
     const float* pvec;  // [param_rows x w]: b_0..b_L, w_o, W_in[:,0] (NAIS-Net: B_l[:,0])

@@ -137,13 +137,13 @@ __device__ __forceinline__ void slab_release(uint64_t* bar, int lane) {
     __syncwarp();
     if (lane == 0) tc::mbar_arrive(bar);
 }
-// Sixteen consecutive floats from a 16-byte-aligned shared-memory address.
 // 8 floats of a read-only table in global memory (L1-cached)
 __device__ __forceinline__ void ld_f8g(const float* src, float* v) {
     const float4 a = __ldg(reinterpret_cast<const float4*>(src)), b = __ldg(reinterpret_cast<const float4*>(src) + 1);
     v[0] = a.x; v[1] = a.y; v[2] = a.z; v[3] = a.w;
     v[4] = b.x; v[5] = b.y; v[6] = b.z; v[7] = b.w;
 }
+// Sixteen consecutive floats from a 16-byte-aligned shared-memory address.
 __device__ __forceinline__ void ld_f16v(const float* src, float (&v)[16]) {
 #pragma unroll
     for (int k = 0; k < 4; ++k) {
@@ -153,29 +153,46 @@ __device__ __forceinline__ void ld_f16v(const float* src, float (&v)[16]) {
 }
 
 // Per-tile blocks of the pipelined kernels (the forward's act' scratch and
-// g_l, the backward's act' and S scratch), 16-column-group-major: the 16
-// BF16 values of columns c0 .. c0+15 (c0 % 16 == 0) of `row` are 32
-// contiguous bytes at word ((c0 / 16) * 128 + row) * 8, so a warp's 32 rows
-// are 1 KB of consecutive memory (two 16-byte accesses per thread).
-__device__ __forceinline__ void st_g16h(uint32_t* blk, int row, int c0, const uint32_t (&u)[8], uint64_t pol) {
-    uint32_t* q = blk + ((size_t)(c0 >> 4) * 128 + row) * 8;
-    asm volatile("st.global.L2::cache_hint.v4.b32 [%0], {%1, %2, %3, %4}, %5;" ::"l"(q), "r"(u[0]), "r"(u[1]),
-                 "r"(u[2]), "r"(u[3]), "l"(pol) : "memory");
-    asm volatile("st.global.L2::cache_hint.v4.b32 [%0], {%1, %2, %3, %4}, %5;" ::"l"(q + 4), "r"(u[4]), "r"(u[5]),
-                 "r"(u[6]), "r"(u[7]), "l"(pol) : "memory");
+// g_l, the backward's act' and S scratch), 8-column-group-major: the 8 BF16
+// values of columns c0 .. c0+7 (c0 % 8 == 0) of `row` are 16 contiguous bytes
+// at word ((c0 / 8) * 128 + row) * 4, so one 16-byte access per thread of a
+// warp covers 512 consecutive bytes (whole 32-byte sectors).
+__device__ __forceinline__ uint32_t* g8_at(uint32_t* blk, int row, int c0) {
+    return blk + ((size_t)(c0 >> 3) * 128 + row) * 4;
 }
-// Columns c0 .. c0+7 (c0 % 8 == 0) of `row`: one half of a 16-column group.
 __device__ __forceinline__ void st_g8h(uint32_t* blk, int row, int c0, const uint32_t (&u)[4], uint64_t pol) {
-    uint32_t* q = blk + ((size_t)(c0 >> 4) * 128 + row) * 8 + ((c0 >> 3) & 1) * 4;
-    asm volatile("st.global.L2::cache_hint.v4.b32 [%0], {%1, %2, %3, %4}, %5;" ::"l"(q), "r"(u[0]), "r"(u[1]),
-                 "r"(u[2]), "r"(u[3]), "l"(pol) : "memory");
+    asm volatile("st.global.L2::cache_hint.v4.b32 [%0], {%1, %2, %3, %4}, %5;" ::"l"(g8_at(blk, row, c0)), "r"(u[0]),
+                 "r"(u[1]), "r"(u[2]), "r"(u[3]), "l"(pol) : "memory");
+}
+// Columns c0 .. c0+15 (c0 % 16 == 0): two 8-column groups.
+__device__ __forceinline__ void st_g16h(uint32_t* blk, int row, int c0, const uint32_t (&u)[8], uint64_t pol) {
+    st_g8h(blk, row, c0, {u[0], u[1], u[2], u[3]}, pol);
+    st_g8h(blk, row, c0 + 8, {u[4], u[5], u[6], u[7]}, pol);
 }
 __device__ __forceinline__ void ld_g16(const uint32_t* blk, int row, int c0, uint32_t (&u)[8]) {
     // through L2 only: L1 keeps the register spills and the parameter table
-    const uint4* q = reinterpret_cast<const uint4*>(blk + ((size_t)(c0 >> 4) * 128 + row) * 8);
-    const uint4 a = __ldcg(q), b = __ldcg(q + 1);
+    const uint4 a = __ldcg(reinterpret_cast<const uint4*>(g8_at(const_cast<uint32_t*>(blk), row, c0)));
+    const uint4 b = __ldcg(reinterpret_cast<const uint4*>(g8_at(const_cast<uint32_t*>(blk), row, c0 + 8)));
     u[0] = a.x; u[1] = a.y; u[2] = a.z; u[3] = a.w;
     u[4] = b.x; u[5] = b.y; u[6] = b.z; u[7] = b.w;
+}
+
+// For each j < 8 the sum of v[j] over the 32 lanes of a warp, by a fixed
+// butterfly (the same additions in the same order on every call): lane l
+// returns the sum for j = (l >> 2) & 7.
+__device__ __forceinline__ float warp_colsum8(const float (&v)[8], int lane) {
+    const bool u16 = lane & 16, u8 = lane & 8, u4 = lane & 4;
+    float a4[4], b2[2];
+#pragma unroll
+    for (int j = 0; j < 4; ++j)
+        a4[j] = (u16 ? v[j + 4] : v[j]) + __shfl_xor_sync(0xffffffffu, u16 ? v[j] : v[j + 4], 16);
+#pragma unroll
+    for (int j = 0; j < 2; ++j)
+        b2[j] = (u8 ? a4[j + 2] : a4[j]) + __shfl_xor_sync(0xffffffffu, u8 ? a4[j] : a4[j + 2], 8);
+    float c = (u4 ? b2[1] : b2[0]) + __shfl_xor_sync(0xffffffffu, u4 ? b2[0] : b2[1], 4);
+    c += __shfl_xor_sync(0xffffffffu, c, 2);
+    c += __shfl_xor_sync(0xffffffffu, c, 1);
+    return c;
 }
 
 // 16 columns (8 packed bf16x2 words) of `row` into a column-pair-major block
@@ -367,7 +384,9 @@ __device__ __forceinline__ void fwdp_body(const FwdZArgs& a, const int cta, cons
         const float* win0 = ptab + (L + 2) * a.w;
         const size_t blk = (size_t)(a.w / 2) * 128;
         uint32_t* scr = a.scratch + (size_t)cta * L * blk;
-        const uint64_t pol_keep = tc::l2_policy_evict_last(), pol_stream = tc::l2_policy_evict_first();
+        // derivative scratch at normal L2 priority: 97 MB over the grid does not fit
+        // beside the streamed stacks, and evict-last measured slower
+        const uint64_t pol_keep = tc::l2_policy_evict_normal(), pol_stream = tc::l2_policy_evict_first();
         bool ok = !a.gate || pwait(&B->gate, 0, budget, abort_flag);
         int tl = 0;
 
@@ -752,7 +771,6 @@ __device__ __forceinline__ void bwdp_body(const BwdArgs& a, const int cta, const
                             tc::tma_store_3d_hint(&a.hb, tile_h + s * 16384, s * 64, t * 128, q, pol_stream);
                             tc::tma_store_3d_hint(&a.hdb, tile_d + s * 16384, s * 64, t * 128, q, pol_stream);
                         } else if (q == L) {
-                            tc::tma_store_3d_hint(&a.hdb, tile_d + s * 16384, s * 64, t * 128, L, pol_stream);
                             tc::tma_store_3d_hint(&a.abb, tile_h + s * 16384, s * 64, t * 128, L, pol_stream);
                         } else {
                             tc::tma_store_3d_hint(&a.abb, tile_h + s * 16384, s * 64, t * 128, 2 * L - q, pol_stream);
@@ -784,7 +802,7 @@ __device__ __forceinline__ void bwdp_body(const BwdArgs& a, const int cta, const
         const size_t blk = (size_t)(a.w / 2) * 128;
         uint32_t* scr_d1 = a.scratch + (size_t)cta * 2 * L * blk;  // act'(a_l), l < L
         uint32_t* scr_S = scr_d1 + (size_t)L * blk;                 // S_l, l < L
-        const uint64_t pol_keep = tc::l2_policy_evict_last();
+        const uint64_t pol_keep = tc::l2_policy_evict_normal();  // as in the forward kernel
         bool ok = !a.gate || pwait(&B->gate, 0, budget, abort_flag);
         int tl = 0;
 
@@ -850,7 +868,7 @@ __device__ __forceinline__ void bwdp_body(const BwdArgs& a, const int cta, const
                             S[j] = f.d2 * ad * g[j];
                             d1[j] = f.d1;
                         }
-                        st_tile8(tile_d, row, cc, hd);
+                        if (!top) st_tile8(tile_d, row, cc, hd);
                         if (!top) {
                             st_tile8(tile_h, row, cc, h);
                             uint32_t w1[4], w2[4];
@@ -862,7 +880,14 @@ __device__ __forceinline__ void bwdp_body(const BwdArgs& a, const int cta, const
                             st_g8h(scr_d1 + (size_t)l * blk, row, cc, w1, pol_keep);
                             st_g8h(scr_S + (size_t)l * blk, row, cc, w2, pol_keep);
                         } else {
-                            if (valid) st_bf16x8(a.HbL + (size_t)p * a.wp + cc, h);
+                            // dw_o = sum over points of alpha h_L + h'_L: this warp's 32 rows
+                            // summed by a fixed butterfly, one partial per tile, row group and
+                            // column (the sum over tiles follows in a fixed order)
+                            float cv[8];
+#pragma unroll
+                            for (int j = 0; j < 8; ++j) cv[j] = valid ? fmaf(alpha_p, h[j], hd[j]) : 0.f;
+                            const float csum = warp_colsum8(cv, lane);
+                            if ((lane & 3) == 0) a.wopart[((size_t)t * 4 + lg) * a.w + cc + ((lane >> 2) & 7)] = csum;
                             float ab[8], hb[8];
 #pragma unroll
                             for (int j = 0; j < 8; ++j) {

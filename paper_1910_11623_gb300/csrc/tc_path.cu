@@ -148,6 +148,7 @@ fbsde_status bf16_create(fbsde_ctx* c) {
         add((size_t)(L > 0 ? L : 1) * b->G_stride * sizeof(bf16));
         add((size_t)b->grid * (2 * L + 2) * 128 * w * sizeof(bf16));
         add((size_t)(2 * L + 3) * w * sizeof(float));
+        add((Pm + 127) / 128 * 4 * (size_t)w * sizeof(float));
     }
     if (b->f8) {
         for (int l = 1; l <= L; ++l) add((size_t)w * b->wp8);
@@ -194,6 +195,7 @@ fbsde_status bf16_create(fbsde_ctx* c) {
         b->G = (bf16*)take((size_t)(L > 0 ? L : 1) * b->G_stride * sizeof(bf16));
         b->scratch = (bf16*)take((size_t)b->grid * (2 * L + 2) * 128 * w * sizeof(bf16));
         b->pvec = (float*)take((size_t)(2 * L + 3) * w * sizeof(float));
+        b->wopart = (float*)take((Pm + 127) / 128 * 4 * (size_t)w * sizeof(float));
     }
     if (b->f8) {
         for (int l = 1; l <= L; ++l) b->W8[l] = (uint8_t*)take((size_t)w * b->wp8);
@@ -654,10 +656,12 @@ static void add_pair(TcArgs& a, const CUtensorMap& A, const CUtensorMap& B, int 
     ++a.npairs;
 }
 
+// Column sums over the P points (or over `rows` rows when given).
 static fbsde_status colsum(fbsde_ctx* c, int cls, const void* X, bool is_bf16, int ldx, int ncols, int mode,
-                           const float* wts, float* out, int ldo, int accumulate, const void* X2 = nullptr) {
+                           const float* wts, float* out, int ldo, int accumulate, const void* X2 = nullptr,
+                           size_t rows = 0) {
     Bf16Work* b = c->bf;
-    const size_t P = c->P();
+    const size_t P = rows ? rows : c->P();
     const size_t chunk = (P + kColSplits - 1) / kColSplits;
     const int splits = (int)((P + chunk - 1) / chunk);
     const float dt = (float)(c->T / c->N);
@@ -948,7 +952,12 @@ fbsde_status bf16_wgrad_tail(fbsde_ctx* c, const float* theta, float* grad) {
         FBSDE_TRY(wgrad(c, ax, D, grad + pl.Win, K0, 1, grad + pl.bin, 1, grad + pl.Win, K0));
     }
     // dw_o = sum_p alpha_p h_L(p) + h'_L(p);  db_o = sum_p alpha_p
-    if (b->fused) {
+    if (b->fused && c->akind != FBSDE_NAIS && !b->f8) {
+        // the pipelined backward left one partial sum per tile, 32-row group
+        // and column: sum them in a fixed order
+        FBSDE_TRY(colsum(c, PROF_WGRAD, b->wopart, false, w, w, 0, nullptr, grad + pl.wo, 1, 0, nullptr,
+                         (P + 127) / 128 * 4));
+    } else if (b->fused) {
         FBSDE_TRY(colsum(c, PROF_WGRAD, b->Hb[L], true, wp, w, 2, c->alpha, grad + pl.wo, 1, 0, b->HDb[L]));
     } else {
         FBSDE_TRY(colsum(c, PROF_WGRAD, b->Hf[L], false, w, w, 2, c->alpha, grad + pl.wo, 1, 0, b->HDf[L]));
