@@ -294,18 +294,13 @@ __device__ __forceinline__ void fwdp_body(const FwdZArgs& a, const int cta, cons
             int it = 0, tl = 0;
             bool ok = !a.gate || pwait(&B->gate, 0, budget, abort_flag);
             const uint32_t tile_addr = tc::smem_u32(tile), ring_addr = tc::smem_u32(ring);
-            const size_t blk = (size_t)(a.w / 2) * 128;
+            // (a bulk L2 prefetch of each reverse phase's act' block measured slower)
             for (int t = cta; ok && t < a.ntiles; t += nctas, ++tl) {
                 for (int q = 0; ok && q < nq; ++q) {
                     const int buf = q & 1;
                     const uint32_t d = tmem + (uint32_t)(buf * 256);
                     const uint32_t idesc = tc::idesc_bf16(128, plan.N(q), 0, 0);
                     const bool accumulate = RES && q > L && q <= 2 * L;
-                    if (q > L && q <= 2 * L) {
-                        // into L2 while this contraction runs: the act' block its epilogue reads
-                        const int l = 2 * L + 1 - q;
-                        tc::prefetch_l2_bulk(a.scratch + ((size_t)cta * L + (l - 1)) * blk, (uint32_t)(blk * 4));
-                    }
                     if (q == 0 && !pwait(&B->xfull, (uint32_t)tl & 1u, budget, abort_flag)) { ok = false; break; }
                     const uint32_t spar = (uint32_t)(tl * (2 * L + 1) + q - 1) & 1u;
                     const int K = plan.K(q);
