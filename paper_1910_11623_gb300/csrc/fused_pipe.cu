@@ -39,6 +39,7 @@
 #include <cuda_bf16.h>
 #include <cuda_runtime.h>
 
+#include <cstddef>
 #include <cstring>
 #include <string>
 #include <type_traits>
@@ -71,24 +72,50 @@ struct PipeBars {
     uint64_t ybar;      // Y partial sums of the four warpgroups are in place (one arrival per warp)
     uint64_t gate;      // never completed: the test hook's first wait
     uint64_t drain;     // MMA issuer: its last contractions have completed
+    uint64_t tread;     // backward: every epilogue warp has read its TMEM columns of an up-sweep phase
     uint32_t tslot;
     int abort_flag;
 };
 
-// Bounded wait that also gives up as soon as another role has aborted.
-__device__ __forceinline__ bool pwait(uint64_t* bar, uint32_t parity, long long budget, volatile int* abort_flag) {
-    if (tc::mbar_try_wait(bar, parity)) return true;
-    const long long t0 = clock64();
+// Bounded wait that also gives up as soon as another role has aborted (the
+// flag's shared-memory address in abort_s).  32-bit clock arithmetic: the
+// control warps run on 32 registers, and a budget below 2^31 cycles (about
+// a second) is exact under one wrap of the counter.
+__device__ __forceinline__ bool try_wait_s(uint32_t bar, uint32_t parity) {
+    uint32_t ok;
+    asm volatile(
+        "{\n\t.reg .pred p;\n\t"
+        "mbarrier.try_wait.parity.shared::cta.b64 p, [%1], %2;\n\t"
+        "selp.u32 %0, 1, 0, p;\n\t}"
+        : "=r"(ok)
+        : "r"(bar), "r"(parity)
+        : "memory");
+    return ok != 0;
+}
+__device__ __forceinline__ bool pwait(uint32_t bar, uint32_t parity, uint32_t budget, uint32_t abort_s) {
+    if (try_wait_s(bar, parity)) return true;
+    const uint32_t t0 = (uint32_t)clock();
     while (true) {
-        if (tc::mbar_try_wait(bar, parity)) return true;
-        if (*abort_flag) return false;
-        if (clock64() - t0 > budget) return false;
+        if (try_wait_s(bar, parity)) return true;
+        uint32_t ab;
+        asm volatile("ld.volatile.shared.u32 %0, [%1];" : "=r"(ab) : "r"(abort_s) : "memory");
+        if (ab) return false;
+        if ((uint32_t)clock() - t0 > budget) return false;
     }
 }
 
-__device__ __forceinline__ void pfail(int* err, volatile int* abort_flag) {
+__device__ __forceinline__ bool pwait(uint64_t* bar, uint32_t parity, uint32_t budget, uint32_t abort_s) {
+    return pwait(tc::smem_u32(bar), parity, budget, abort_s);
+}
+
+__device__ __forceinline__ void pfail(int* err, uint32_t abort_s) {
     if (err) atomicExch(err, 2);
-    *abort_flag = 1;
+    asm volatile("st.volatile.shared.u32 [%0], %1;" ::"r"(abort_s), "r"(1u) : "memory");
+}
+
+// A wait budget for pwait (at most 2^31 - 1 cycles).
+__host__ __device__ __forceinline__ uint32_t pbudget(long long b) {
+    return (uint32_t)(b < 0x7fffffffLL ? (b > 0 ? b : 0) : 0x7fffffffLL);
 }
 
 // The waits at the end, for asynchronous work already issued: bounded, and
@@ -232,13 +259,13 @@ __device__ __forceinline__ void fwdp_body(const FwdZArgs& a, const int cta, cons
     const int prows = param_rows(L, 0);
     float* ysum = ptab + prows * a.w;
     PipeBars* B = (PipeBars*)(((uintptr_t)(ysum + kPGroups * 128) + 15) & ~(uintptr_t)15);
-    volatile int* abort_flag = &B->abort_flag;
+    const uint32_t abort_s = tc::smem_u32(&B->abort_flag);
 
     const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
     const PipeFwdPlan plan{&a};
     const int nq = plan.nq();
     const int nkw = a.wp / 64;
-    const long long budget = a.wait_budget;
+    const uint32_t budget = pbudget(a.wait_budget);
 
     stage_params(ptab, a.theta, a.off, L, a.w, a.D + 1);
     if (threadIdx.x == 0) {
@@ -270,14 +297,14 @@ __device__ __forceinline__ void fwdp_body(const FwdZArgs& a, const int cta, cons
         if (warp == 0 && lane == 0) {
             // ---- producer: the weight slices of every phase through the ring
             int it = 0;
-            bool ok = !a.gate || pwait(&B->gate, 0, budget, abort_flag);
+            bool ok = !a.gate || pwait(&B->gate, 0, budget, abort_s);
             for (int t = cta; ok && t < a.ntiles; t += nctas)
                 for (int q = 0; ok && q < nq; ++q) {
                     const CUtensorMap* m = plan.map(q);
                     const uint32_t bytes = (uint32_t)plan.N(q) * 128u;
                     for (int kc = 0; kc < plan.nk(q); ++kc, ++it) {
                         const int s = it % kPStages;
-                        if (!pwait(&B->bempty[s], ((uint32_t)(it / kPStages) & 1u) ^ 1u, budget, abort_flag)) {
+                        if (!pwait(&B->bempty[s], ((uint32_t)(it / kPStages) & 1u) ^ 1u, budget, abort_s)) {
                             ok = false;
                             break;
                         }
@@ -285,14 +312,14 @@ __device__ __forceinline__ void fwdp_body(const FwdZArgs& a, const int cta, cons
                         tc::tma_load_2d(ring + s * kFStageBytes, m, &B->bfull[s], kc * 64, 0);
                     }
                 }
-            if (!ok) pfail(a.err, abort_flag);
+            if (!ok) pfail(a.err, abort_s);
             // drain: the loads of the last stages issued
             for (int j = it - 1; j >= 0 && j >= it - kPStages; --j)
                 tc::mbar_wait(&B->bfull[j % kPStages], (uint32_t)(j / kPStages) & 1u, kDrainBudget);
         } else if (warp == 1 && lane == 0) {
             // ---- MMA issuer
             int it = 0, tl = 0;
-            bool ok = !a.gate || pwait(&B->gate, 0, budget, abort_flag);
+            bool ok = !a.gate || pwait(&B->gate, 0, budget, abort_s);
             const uint32_t tile_addr = tc::smem_u32(tile), ring_addr = tc::smem_u32(ring);
             // (a bulk L2 prefetch of each reverse phase's act' block measured slower)
             for (int t = cta; ok && t < a.ntiles; t += nctas, ++tl) {
@@ -301,36 +328,41 @@ __device__ __forceinline__ void fwdp_body(const FwdZArgs& a, const int cta, cons
                     const uint32_t d = tmem + (uint32_t)(buf * 256);
                     const uint32_t idesc = tc::idesc_bf16(128, plan.N(q), 0, 0);
                     const bool accumulate = RES && q > L && q <= 2 * L;
-                    if (q == 0 && !pwait(&B->xfull, (uint32_t)tl & 1u, budget, abort_flag)) { ok = false; break; }
+                    if (q == 0 && !pwait(&B->xfull, (uint32_t)tl & 1u, budget, abort_s)) { ok = false; break; }
                     const uint32_t spar = (uint32_t)(tl * (2 * L + 1) + q - 1) & 1u;
                     const int K = plan.K(q);
                     for (int kc = 0; kc < plan.nk(q); ++kc, ++it) {
                         const int s = it % kPStages;
-                        if (!pwait(&B->bfull[s], (uint32_t)(it / kPStages) & 1u, budget, abort_flag) ||
-                            (q > 0 && !pwait(&B->slab[kc], spar, budget, abort_flag))) {
+                        if (!pwait(&B->bfull[s], (uint32_t)(it / kPStages) & 1u, budget, abort_s) ||
+                            (q > 0 && !pwait(&B->slab[kc], spar, budget, abort_s))) {
                             ok = false;
                             break;
                         }
                         tc::tc_fence_after();
                         const int nsteps = min(4, (K - kc * 64 + 15) / 16);
-                        for (int k = 0; k < nsteps; ++k) {
-                            const uint64_t ad = tc::sdesc_sw128(tile_addr + (uint32_t)kc * 16384u + 32u * k, 16u);
-                            const uint64_t bd = tc::sdesc_sw128(ring_addr + (uint32_t)s * kFStageBytes + 32u * k, 16u);
-                            tc::mma_bf16(d, ad, bd, idesc, (accumulate || kc > 0 || k > 0) ? 1u : 0u);
+                        // four K steps unrolled, the ones past K skipped (a loop with a
+                        // run-time trip count spills this role's registers)
+#pragma unroll
+                        for (int k = 0; k < 4; ++k) {
+                            if (k < nsteps) {
+                                const uint64_t ad = tc::sdesc_sw128(tile_addr + (uint32_t)kc * 16384u + 32u * k, 16u);
+                                const uint64_t bd = tc::sdesc_sw128(ring_addr + (uint32_t)s * kFStageBytes + 32u * k, 16u);
+                                tc::mma_bf16(d, ad, bd, idesc, (accumulate || kc > 0 || k > 0) ? 1u : 0u);
+                            }
                         }
                         tc::mma_commit(&B->bempty[s]);
                     }
                     if (ok) tc::mma_commit(&B->accf[buf]);
                 }
             }
-            if (!ok) pfail(a.err, abort_flag);
+            if (!ok) pfail(a.err, abort_s);
             // drain: every contraction issued has completed
             tc::mma_commit(&B->drain);
             tc::mbar_wait(&B->drain, 0, kDrainBudget);
         } else if (warp == 2 && lane == 0) {
             // ---- store warp: operand-stack stores, input rows, tile release
             const uint64_t pol_stream = tc::l2_policy_evict_first();
-            bool ok = !a.gate || pwait(&B->gate, 0, budget, abort_flag);
+            bool ok = !a.gate || pwait(&B->gate, 0, budget, abort_s);
             int tl = 0, xl = 0;  // tiles processed, input loads issued
             auto load_x = [&](int t) {
                 tc::mbar_expect_tx(&B->xfull, (uint32_t)(a.Dp / 64) * 16384u);
@@ -347,7 +379,7 @@ __device__ __forceinline__ void fwdp_body(const FwdZArgs& a, const int cta, cons
                     const uint32_t par = (uint32_t)(tl * (2 * L + 1) + q) & 1u;
                     const bool store = a.for_grad && q >= L;
                     for (int s = 0; s < nkw; ++s) {
-                        if (!pwait(&B->slab[s], par, budget, abort_flag)) { ok = false; break; }
+                        if (!pwait(&B->slab[s], par, budget, abort_s)) { ok = false; break; }
                         if (store) {
                             tc::tma_store_3d_hint(&a.eb, tile + s * 16384, s * 64, t * 128, 2 * L - q, pol_stream);
                             tc::tma_store_commit();
@@ -361,10 +393,10 @@ __device__ __forceinline__ void fwdp_body(const FwdZArgs& a, const int cta, cons
                 // the Z contraction reads e_0 from the tile; the next tile's
                 // input rows replace it once that contraction has completed
                 const uint32_t zpar = (uint32_t)((tl * nq + 2 * L + 1) >> 1) & 1u;
-                if (!pwait(&B->accf[1], zpar, budget, abort_flag)) { ok = false; break; }
+                if (!pwait(&B->accf[1], zpar, budget, abort_s)) { ok = false; break; }
                 if (t + nctas < a.ntiles) load_x(t + nctas);
             }
-            if (!ok) pfail(a.err, abort_flag);
+            if (!ok) pfail(a.err, abort_s);
             // drain: bulk stores, and the last input load if nobody consumed it
             tc::tma_store_wait_all<0>();
             if (xl > 0) tc::mbar_wait(&B->xfull, (uint32_t)(xl - 1) & 1u, kDrainBudget);
@@ -382,15 +414,15 @@ __device__ __forceinline__ void fwdp_body(const FwdZArgs& a, const int cta, cons
         // derivative scratch at normal L2 priority: 97 MB over the grid does not fit
         // beside the streamed stacks, and evict-last measured slower
         const uint64_t pol_keep = tc::l2_policy_evict_normal(), pol_stream = tc::l2_policy_evict_first();
-        bool ok = !a.gate || pwait(&B->gate, 0, budget, abort_flag);
+        bool ok = !a.gate || pwait(&B->gate, 0, budget, abort_s);
         int tl = 0;
 
         // wait for contraction q (TMEM buffer q % 2) and, when the phase writes
         // the operand tile, for the tile's release
         auto begin = [&](int q) -> bool {
-            if (!pwait(&B->accf[q & 1], (uint32_t)((tl * nq + q) >> 1) & 1u, budget, abort_flag)) return false;
+            if (!pwait(&B->accf[q & 1], (uint32_t)((tl * nq + q) >> 1) & 1u, budget, abort_s)) return false;
             tc::tc_fence_after();
-            if (q <= 2 * L && !pwait(&B->tfree, (uint32_t)(tl * (2 * L + 1) + q) & 1u, budget, abort_flag))
+            if (q <= 2 * L && !pwait(&B->tfree, (uint32_t)(tl * (2 * L + 1) + q) & 1u, budget, abort_s))
                 return false;
             return true;
         };
@@ -540,7 +572,7 @@ __device__ __forceinline__ void fwdp_body(const FwdZArgs& a, const int cta, cons
             __syncwarp();
             if (lane == 0) tc::mbar_arrive(&B->ybar);
             if (eg == 0) {
-                if (!(ok = pwait(&B->ybar, (uint32_t)tl & 1u, budget, abort_flag))) break;
+                if (!(ok = pwait(&B->ybar, (uint32_t)tl & 1u, budget, abort_s))) break;
                 float y = __ldg(a.theta + a.off.bo);
                 for (int g2 = 0; g2 < kPGroups; ++g2) y += ysum[g2 * 128 + row];
                 if (valid) a.Y[p] = y;
@@ -572,7 +604,7 @@ __device__ __forceinline__ void fwdp_body(const FwdZArgs& a, const int cta, cons
                 }
             }
         }
-        if (!ok) pfail(a.err, abort_flag);
+        if (!ok) pfail(a.err, abort_s);
     }
 
     tc::tc_fence_before();
@@ -626,13 +658,13 @@ __device__ __forceinline__ void bwdp_body(const BwdArgs& a, const int cta, const
     const float* ptab = a.pvec;
     const int L = a.L;
     PipeBars* B = (PipeBars*)(ring + kPBwdStages * kFStageBytes);
-    volatile int* abort_flag = &B->abort_flag;
+    const uint32_t abort_s = tc::smem_u32(&B->abort_flag);
 
     const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
     const PipeBwdPlan plan{&a};
     const int nq = plan.nq();
     const int nkw = a.wp / 64, nkx = a.Dp / 64;
-    const long long budget = a.wait_budget;
+    const uint32_t budget = pbudget(a.wait_budget);
 
     if (threadIdx.x == 0) {
         for (int s = 0; s < kPBwdStages; ++s) {
@@ -644,6 +676,7 @@ __device__ __forceinline__ void bwdp_body(const BwdArgs& a, const int cta, const
         tc::mbar_init(&B->tfree, 1);
         tc::mbar_init(&B->xfull, 1);
         tc::mbar_init(&B->ybar, 1);  // the tangent inputs (v rows) of a tile have arrived
+        tc::mbar_init(&B->tread, 4 * kPGroups);
         tc::mbar_init(&B->gate, 1);
         tc::mbar_init(&B->drain, 1);
         B->abort_flag = 0;
@@ -664,14 +697,20 @@ __device__ __forceinline__ void bwdp_body(const BwdArgs& a, const int cta, const
         if (warp == 0 && lane == 0) {
             // ---- producer
             int it = 0;
-            bool ok = !a.gate || pwait(&B->gate, 0, budget, abort_flag);
+            bool ok = !a.gate || pwait(&B->gate, 0, budget, abort_s);
             for (int t = cta; ok && t < a.ntiles; t += nctas)
                 for (int q = 0; ok && q < nq; ++q) {
+                    if (q < L) {
+                        // into L2 about one phase ahead of its reader: g_q, read by the
+                        // epilogue of up-sweep phase q
+                        const size_t blk = (size_t)(a.w / 2) * 128;
+                        tc::prefetch_l2_bulk(a.G + (size_t)q * a.G_words + (size_t)t * blk, (uint32_t)(blk * 4));
+                    }
                     const CUtensorMap* m = plan.map(q);
                     const uint32_t bytes = (uint32_t)a.w * 128u;
                     for (int kc = 0; kc < plan.nk(q); ++kc, ++it) {
                         const int s = it % kPBwdStages;
-                        if (!pwait(&B->bempty[s], ((uint32_t)(it / kPBwdStages) & 1u) ^ 1u, budget, abort_flag)) {
+                        if (!pwait(&B->bempty[s], ((uint32_t)(it / kPBwdStages) & 1u) ^ 1u, budget, abort_s)) {
                             ok = false;
                             break;
                         }
@@ -679,69 +718,79 @@ __device__ __forceinline__ void bwdp_body(const BwdArgs& a, const int cta, const
                         tc::tma_load_2d(ring + s * kFStageBytes, m, &B->bfull[s], kc * 64, 0);
                     }
                 }
-            if (!ok) pfail(a.err, abort_flag);
+            if (!ok) pfail(a.err, abort_s);
             for (int j = it - 1; j >= 0 && j >= it - kPBwdStages; --j)
                 tc::mbar_wait(&B->bfull[j % kPBwdStages], (uint32_t)(j / kPBwdStages) & 1u, kDrainBudget);
         } else if (warp == 1 && lane == 0) {
-            // ---- MMA issuer
+            // ---- MMA issuer (few live values: the control warps run on 32
+            // registers, and a spilled value reloaded after a long wait costs a
+            // round trip to L2)
             int it = 0, tl = 0;
-            bool ok = !a.gate || pwait(&B->gate, 0, budget, abort_flag);
-            const uint32_t th_addr = tc::smem_u32(tile_h), td_addr = tc::smem_u32(tile_d);
-            const uint32_t ring_addr = tc::smem_u32(ring);
+            bool ok = !a.gate || pwait(&B->gate, 0, budget, abort_s);
             const uint32_t idesc = tc::idesc_bf16(128, a.w, 0, 0);
+            // shared-memory descriptors: the fields but the start address, and
+            // start addresses in 16-byte units (+2 per 16-element K step)
+            const uint64_t dfix = tc::sdesc_sw128(0u, 16u);
+            const uint32_t th16 = tc::smem_u32(tile_h) >> 4, td16 = tc::smem_u32(tile_d) >> 4;
+            const uint32_t rg16 = tc::smem_u32(ring) >> 4;
+            // barrier addresses in shared memory (32 bits)
+            const uint32_t Bs = tc::smem_u32(B);
+            const uint32_t bfull_s = Bs + (uint32_t)offsetof(PipeBars, bfull), slab_s = Bs + (uint32_t)offsetof(PipeBars, slab);
             for (int t = cta; ok && t < a.ntiles; t += nctas, ++tl) {
                 for (int q = 0; ok && q < nq; ++q) {
-                    const int G = tl * nq + q;
                     const bool up = q <= L;
-                    const uint32_t d = tmem + (uint32_t)((up ? 0 : (q & 1)) * 256);
-                    const bool accumulate = RES && !up;
-                    const uint32_t spar = (uint32_t)(G - 1) & 1u;
+                    const uint32_t spar = (uint32_t)(tl * nq + q - 1) & 1u;
                     if (q == 0) {
-                        if (!pwait(&B->xfull, (uint32_t)tl & 1u, budget, abort_flag) ||
-                            !pwait(vfull, (uint32_t)tl & 1u, budget, abort_flag)) { ok = false; break; }
-                    } else if (q <= L + 1) {
-                        // the contraction overwrites both accumulators (or accumulates
-                        // onto the seeded adjoint): every slab of the last phase done
-                        for (int s = 0; s < nkw && ok; ++s) ok = pwait(&B->slab[s], spar, budget, abort_flag);
+                        if (!pwait(&B->xfull, (uint32_t)tl & 1u, budget, abort_s) ||
+                            !pwait(vfull, (uint32_t)tl & 1u, budget, abort_s)) { ok = false; break; }
+                    } else if (up) {
+                        // the contraction overwrites both accumulators: every epilogue
+                        // warp of the last phase has read them (each K slice then waits
+                        // for its slab of the operand tiles below), so the first K
+                        // slices run while the last slab is still being computed
+                        if (!pwait(Bs + (uint32_t)offsetof(PipeBars, tread), (uint32_t)(tl * L + q - 1) & 1u, budget, abort_s)) { ok = false; break; }
+                    } else if (q == L + 1) {
+                        // accumulates onto the adjoint the top phase seeded: every slab done
+                        for (int s = 0; s < nkw && ok; ++s) ok = pwait(slab_s + 8u * s, spar, budget, abort_s);
                         if (!ok) break;
                     }
-                    const int K = plan.K(q);
-                    for (int kc = 0; kc < plan.nk(q); ++kc, ++it) {
+                    const uint32_t d = tmem + (up ? 0u : (uint32_t)((q & 1) * 256));
+                    const bool kslab = q >= 1 && q != L + 1;
+                    const int nk = plan.nk(q), K = plan.K(q);
+                    for (int kc = 0; kc < nk; ++kc, ++it) {
                         const int s = it % kPBwdStages;
-                        if (!pwait(&B->bfull[s], (uint32_t)(it / kPBwdStages) & 1u, budget, abort_flag) ||
-                            (q > L + 1 && !pwait(&B->slab[kc], spar, budget, abort_flag))) {
+                        if (!pwait(bfull_s + 8u * s, (uint32_t)(it / kPBwdStages) & 1u, budget, abort_s) ||
+                            (kslab && !pwait(slab_s + 8u * kc, spar, budget, abort_s))) {
                             ok = false;
                             break;
                         }
                         tc::tc_fence_after();
                         const int nsteps = min(4, (K - kc * 64 + 15) / 16);
-                        for (int k = 0; k < nsteps; ++k) {
-                            const uint64_t bd = tc::sdesc_sw128(ring_addr + (uint32_t)s * kFStageBytes + 32u * k, 16u);
-                            const uint64_t ah = tc::sdesc_sw128(th_addr + (uint32_t)kc * 16384u + 32u * k, 16u);
-                            const uint32_t en = (accumulate || kc > 0 || k > 0) ? 1u : 0u;
-                            tc::mma_bf16(d, ah, bd, idesc, en);
-                            if (up) {
-                                const uint64_t ad = tc::sdesc_sw128(td_addr + (uint32_t)kc * 16384u + 32u * k, 16u);
-                                tc::mma_bf16(tmem + 256u, ad, bd, idesc, (kc > 0 || k > 0) ? 1u : 0u);
+                        const uint32_t b16 = rg16 + (uint32_t)s * (kFStageBytes >> 4);
+                        const uint32_t a16 = (uint32_t)kc * (16384u >> 4);
+                        // four K steps unrolled, the ones past K skipped (a loop with a
+                        // run-time trip count spills this role's registers)
+#pragma unroll
+                        for (int k = 0; k < 4; ++k) {
+                            if (k < nsteps) {
+                                const uint32_t en = ((!up && RES) || kc > 0 || k > 0) ? 1u : 0u;
+                                const uint64_t bd = dfix | (b16 + 2u * k);
+                                tc::mma_bf16(d, dfix | (th16 + a16 + 2u * k), bd, idesc, en);
+                                if (up) tc::mma_bf16(tmem + 256u, dfix | (td16 + a16 + 2u * k), bd, idesc, en);
                             }
                         }
                         tc::mma_commit(&B->bempty[s]);
                     }
-                    if (ok) tc::mma_commit(&B->accf[G & 1]);
-                    if (ok && q + 1 < L) {
-                        // into L2 while this contraction runs: g_{q+1}, read by the next phase
-                        const size_t blk = (size_t)(a.w / 2) * 128;
-                        tc::prefetch_l2_bulk(a.G + (size_t)(q + 1) * a.G_words + (size_t)t * blk, (uint32_t)(blk * 4));
-                    }
+                    if (ok) tc::mma_commit(&B->accf[(tl * nq + q) & 1]);
                 }
             }
-            if (!ok) pfail(a.err, abort_flag);
+            if (!ok) pfail(a.err, abort_s);
             tc::mma_commit(&B->drain);
             tc::mbar_wait(&B->drain, 0, kDrainBudget);
         } else if (warp == 2 && lane == 0) {
             // ---- store warp: operand-stack stores, input rows, tile release
             const uint64_t pol_stream = tc::l2_policy_evict_first();
-            bool ok = !a.gate || pwait(&B->gate, 0, budget, abort_flag);
+            bool ok = !a.gate || pwait(&B->gate, 0, budget, abort_s);
             int tl = 0, xl = 0, vl = 0;
             auto load_x = [&](int t) {
                 tc::mbar_expect_tx(&B->xfull, (uint32_t)nkx * 16384u);
@@ -761,7 +810,7 @@ __device__ __forceinline__ void bwdp_body(const BwdArgs& a, const int cta, const
                 for (int q = 0; ok && q < nq; ++q) {
                     const uint32_t par = (uint32_t)(tl * nq + q) & 1u;
                     for (int s = 0; s < nkw; ++s) {
-                        if (!pwait(&B->slab[s], par, budget, abort_flag)) { ok = false; break; }
+                        if (!pwait(&B->slab[s], par, budget, abort_s)) { ok = false; break; }
                         if (q < L) {
                             tc::tma_store_3d_hint(&a.hb, tile_h + s * 16384, s * 64, t * 128, q, pol_stream);
                             tc::tma_store_3d_hint(&a.hdb, tile_d + s * 16384, s * 64, t * 128, q, pol_stream);
@@ -782,7 +831,7 @@ __device__ __forceinline__ void bwdp_body(const BwdArgs& a, const int cta, const
                     tc::mbar_arrive(&B->tfree);
                 }
             }
-            if (!ok) pfail(a.err, abort_flag);
+            if (!ok) pfail(a.err, abort_s);
             tc::tma_store_wait_all<0>();
             if (xl > 0) tc::mbar_wait(&B->xfull, (uint32_t)(xl - 1) & 1u, kDrainBudget);
             if (vl > 0) tc::mbar_wait(vfull, (uint32_t)(vl - 1) & 1u, kDrainBudget);
@@ -798,14 +847,14 @@ __device__ __forceinline__ void bwdp_body(const BwdArgs& a, const int cta, const
         uint32_t* scr_d1 = a.scratch + (size_t)cta * 2 * L * blk;  // act'(a_l), l < L
         uint32_t* scr_S = scr_d1 + (size_t)L * blk;                 // S_l, l < L
         const uint64_t pol_keep = tc::l2_policy_evict_normal();  // as in the forward kernel
-        bool ok = !a.gate || pwait(&B->gate, 0, budget, abort_flag);
+        bool ok = !a.gate || pwait(&B->gate, 0, budget, abort_s);
         int tl = 0;
 
         auto begin = [&](int q) -> bool {
             const int G = tl * nq + q;
-            if (!pwait(&B->accf[G & 1], (uint32_t)(G >> 1) & 1u, budget, abort_flag)) return false;
+            if (!pwait(&B->accf[G & 1], (uint32_t)(G >> 1) & 1u, budget, abort_s)) return false;
             tc::tc_fence_after();
-            return pwait(&B->tfree, (uint32_t)G & 1u, budget, abort_flag);
+            return pwait(&B->tfree, (uint32_t)G & 1u, budget, abort_s);
         };
 
         // up-sweep layer l: a = acc + b_l (+ t W_in[:,0]), t = act(a):
@@ -831,6 +880,13 @@ __device__ __forceinline__ void bwdp_body(const BwdArgs& a, const int cta, const
                     tc::tmem_ld8(tlane + (uint32_t)cc, ra);
                     tc::tmem_ld8(tlane + 256u + (uint32_t)cc, rt);
                     tc::tmem_wait_ld();
+                    if (!top && half == 1 && s == nkw - 1) {
+                        // this warp's last TMEM read of the phase: the next contraction may
+                        // overwrite the accumulators
+                        tc::tc_fence_before();
+                        __syncwarp();
+                        if (lane == 0) tc::mbar_arrive(&B->tread);
+                    }
                     if (c0 < a.w) {
                         float bv[8], g[8], hp[8], hdp[8];
                         ld_f8g(bias + cc, bv);
@@ -963,7 +1019,7 @@ __device__ __forceinline__ void bwdp_body(const BwdArgs& a, const int cta, const
             for (int l = 1; ok && l <= L; ++l) ok = up(std::false_type{}, l, tval, alpha_p, t, valid, p);
             for (int q = L + 1; ok && q <= 2 * L; ++q) ok = adj(q);
         }
-        if (!ok) pfail(a.err, abort_flag);
+        if (!ok) pfail(a.err, abort_s);
     }
 
     tc::tc_fence_before();
