@@ -51,7 +51,7 @@ namespace fbsde {
 constexpr int kPGroups = 4;                      // epilogue warpgroups
 constexpr int kPThreads = 128 * (1 + kPGroups);  // warpgroup 0: producer, MMA, store warp, spare
 constexpr int kPStages = 3;                      // weight ring stages of the forward kernel (32 KB each)
-constexpr int kPBwdStages = 2;                   // the backward kernel's two operand tiles leave room for two
+constexpr int kPBwdStages = 3;                   // the backward kernel's ring (its two operand tiles take 128 KB)
 // 20 warps: 5 per SM sub-partition, 96 registers per thread at launch;
 // warpgroup 0 then drops to kPRegsCtl and the epilogue warpgroups rise to
 // kPRegsEpi (setmaxnreg).
@@ -64,7 +64,7 @@ static_assert(16384 / ((kPThreads / 32 + 3) / 4 * 32) >= kPRegsLaunch, "launch r
 
 // Barriers and flags of one CTA (shared memory).
 struct PipeBars {
-    uint64_t bfull[kPStages], bempty[kPStages];  // weight ring
+    uint64_t bfull[kPStages > kPBwdStages ? kPStages : kPBwdStages], bempty[kPStages > kPBwdStages ? kPStages : kPBwdStages];
     uint64_t accf[2];   // contraction into TMEM buffer b complete
     uint64_t slab[4];   // 64-column slab s of the operand tile written (one arrival per epilogue warp)
     uint64_t tfree;     // the operand tile may be written by the next phase (store warp)
@@ -653,8 +653,9 @@ __device__ __forceinline__ void bwdp_body(const BwdArgs& a, const int cta, const
     uint8_t* tile_d = smem + kFTileBytes;    // h'_l
     uint8_t* ring = smem + 2 * kFTileBytes;
     // the per-column parameters are read from the table in global memory (held
-    // in L1): without a copy in shared memory the kernel fits the 196 KB
-    // shared-memory configuration, which leaves 60 KB of L1
+    // in L1): shared memory holds the two operand tiles and a ring of three
+    // weight slices, so the contraction of an up-sweep phase finds its first
+    // three K slices loaded
     const float* ptab = a.pvec;
     const int L = a.L;
     PipeBars* B = (PipeBars*)(ring + kPBwdStages * kFStageBytes);
@@ -1057,8 +1058,8 @@ static cudaError_t prepare_pipe(K kernel, size_t smem) {
     cudaError_t e = cudaFuncSetAttribute(kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
     if (e != cudaSuccess) return e;
     // the smallest shared-memory configuration that holds the block (196 of 228
-    // KB when it fits): the rest of the SM's 256 KB is L1, which keeps the
-    // epilogue's register spills close
+    // KB when it fits, as for the forward kernel): the rest of the SM's 256 KB
+    // is L1
     e = cudaFuncSetAttribute(kernel, cudaFuncAttributePreferredSharedMemoryCarveout, 85);
     if (e != cudaSuccess) return e;
     // the register split assumes exactly kPRegsLaunch registers per thread at launch
