@@ -184,8 +184,10 @@ def fused_algorithmic_bytes(w):
     """Bytes one fused forward and one fused backward launch must move (their
     mean), or None when the workload is not served by the fused kernels.
     Forward: the e_l (L + 1) and g_l (L) BF16 operand blocks, Z and Y written,
-    the BF16 X rows read.  Backward: h'_l, h_l and abar_l (3 (L + 1) blocks)
-    written, the g_l blocks and the BF16 X and v rows read."""
+    the BF16 X rows read.  Backward: the g_l blocks and the BF16 X and v rows
+    read; written, for FC / ResNet (the pipelined kernel) h'_l and h_l for
+    l < L and abar_l for l <= L (3L + 1 blocks) and the read-out gradient's
+    per-tile partial sums, for NAIS-Net h'_l, h_l and abar_l (3 (L + 1))."""
     p, a = w.problem, w.arch
     if a.prec == "fp32" or a.width > 256 or a.depth > 8 or p.D > 256:
         return None
@@ -193,7 +195,10 @@ def fused_algorithmic_bytes(w):
     stack = P * (-(-a.width // 64) * 64) * 2
     rows = P * (-(-p.D // 64) * 64) * 2
     fwd = (2 * L + 1) * stack + rows + P * p.D * 4 + P * 4
-    bwd = 3 * (L + 1) * stack + L * stack + 2 * rows
+    if a.kind == "nais" or a.prec not in ("bf16", None):
+        bwd = 3 * (L + 1) * stack + L * stack + 2 * rows
+    else:
+        bwd = (3 * L + 1) * stack + L * stack + 2 * rows + (-(-P // 128)) * 4 * a.width * 4
     return (fwd + bwd) / 2.0
 
 
