@@ -295,6 +295,8 @@ __global__ void k_resid(ProblemDev pd, const float* __restrict__ X, const float*
     const float* x = X + p * D;
     const float* z = Z + p * D;
     const float* w = dW + p * D;
+    // Y_n and Y_{n+1} requested with the quads below, not after the sums
+    const float yn = Y[p], yn1 = Y[p + pd.M];
     // quad q of this point: x, z and dW of dimensions 4q .. 4q+3 (zero past D)
     auto quad = [&](int q, float (&xv)[4], float (&zv)[4], float (&dw)[4]) {
         const int d0 = 4 * q;
@@ -332,7 +334,6 @@ __global__ void k_resid(ProblemDev pd, const float* __restrict__ X, const float*
         }
     }
     zx = warp_sum(zx); zsdw = warp_sum(zsdw); zz = warp_sum(zz);
-    const float yn = Y[p], yn1 = Y[p + pd.M];
     const float phi = bsb ? pd.r * (yn - zx) : zz;
     const float r = yn1 - yn - phi * pd.dt - zsdw;
     if (lane == 0) rbuf[p] = r;

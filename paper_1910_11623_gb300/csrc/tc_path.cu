@@ -609,26 +609,36 @@ __global__ void k_colsum_reduce(const float* __restrict__ part, int splits, int 
     if (lane == 0) out[(size_t)c * ldo] = accumulate ? out[(size_t)c * ldo] + s : s;
 }
 
-// out[r * ld + off + c] = sum_z part[z][r][c] for c < nc: thread per output,
-// splits summed in order with four independent partial sums combined in a
-// fixed order (bit-reproducible).
-__global__ void k_reduce_split(const float* __restrict__ part, int splits, int rows, int N, int nc,
-                               float* __restrict__ out, int ld, int off) {
-    const int i = blockIdx.x * blockDim.x + threadIdx.x;
-    if (i >= rows * nc) return;
-    const int r = i / nc, cc = i % nc;
+// out[r * ld + off + c] = sum_z part[z][r][c] for c < nc.  A block takes 32
+// consecutive columns of one row: warp g sums the splits z = g, g + 8, ...
+// for its 32 columns (one column per lane, every load in flight at once), and
+// warp 0 adds the eight warps' sums in order (bit-reproducible).
+__global__ void __launch_bounds__(256) k_reduce_split(const float* __restrict__ part, int splits, int rows, int N,
+                                                      int nc, float* __restrict__ out, int ld, int off) {
+    __shared__ float red[8][33];
+    const int lane = threadIdx.x & 31, g = threadIdx.x >> 5;
+    const int cblocks = (nc + 31) / 32;
+    const int r = blockIdx.x / cblocks, c = (blockIdx.x % cblocks) * 32 + lane;
     const size_t stride = (size_t)rows * N;
-    const float* q = part + (size_t)r * N + cc;
-    float s0 = 0.f, s1 = 0.f, s2 = 0.f, s3 = 0.f;
-    int z = 0;
-    for (; z + 3 < splits; z += 4) {
-        s0 += q[(size_t)z * stride];
-        s1 += q[(size_t)(z + 1) * stride];
-        s2 += q[(size_t)(z + 2) * stride];
-        s3 += q[(size_t)(z + 3) * stride];
+    float s = 0.f;
+    if (r < rows && c < nc) {
+        const float* q = part + (size_t)r * N + c;
+        int z = g;
+        for (; z + 24 < splits; z += 32) {
+            const float a0 = __ldcs(q + (size_t)z * stride), a1 = __ldcs(q + (size_t)(z + 8) * stride);
+            const float a2 = __ldcs(q + (size_t)(z + 16) * stride), a3 = __ldcs(q + (size_t)(z + 24) * stride);
+            s += (a0 + a1) + (a2 + a3);
+        }
+        for (; z < splits; z += 8) s += __ldcs(q + (size_t)z * stride);
     }
-    for (; z < splits; ++z) s0 += q[(size_t)z * stride];
-    out[(size_t)r * ld + off + cc] = (s0 + s1) + (s2 + s3);
+    red[g][lane] = s;
+    __syncthreads();
+    if (g == 0 && r < rows && c < nc) {
+        float t = red[0][lane];
+#pragma unroll
+        for (int k = 1; k < 8; ++k) t += red[k][lane];
+        out[(size_t)r * ld + off + c] = t;
+    }
 }
 
 // ------------------------------------------------------------------ launch helpers
@@ -712,7 +722,7 @@ static fbsde_status wgrad(fbsde_ctx* c, TcArgs a, int ncols_store, float* out, i
     double flops = 0;
     for (int q = 0; q < a.npairs; ++q) flops += 2.0 * a.rows * (double)ncols_store * P;
     FBSDE_TRY(tc_launch<true>(c, PROF_WGRAD, a, splits, EpiPartB{c->part, a.rows, a.N}, flops));
-    k_reduce_split<<<nblk((size_t)a.rows * ncols_store, 256), 256, 0, c->stream>>>(c->part, splits, a.rows, a.N,
+    k_reduce_split<<<(unsigned)(a.rows * ((ncols_store + 31) / 32)), 256, 0, c->stream>>>(c->part, splits, a.rows, a.N,
                                                                                    ncols_store, out, ld, off);
     FBSDE_CK_LAUNCH(c);
     if (cs) {
