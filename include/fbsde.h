@@ -247,8 +247,10 @@ fbsde_status fbsde_graph_destroy(fbsde_graph* graph);
  * or device arrays of n floats (instance i writes index i).  On return the
  * group's stream is ordered after all of them.  In FBSDE_GROUP_GROUPED mode
  * (the default) the instances served by the fused BF16 kernels with the same
- * kernel variant (activation and network kind; FP8 forms excluded), when
- * there are at least two, run their forward kernels as one persistent launch
+ * kernel variant (activation and network kind; FP8 forms excluded) and at
+ * most two 128-point tiles per SM (a larger instance fills the GPU alone and
+ * runs its whole step on its own stream), when there are at least two, run
+ * their forward kernels as one persistent launch
  * and their backward kernels as one more, instance i on its own range of
  * CTAs (its grid cap, one per SM when unset); their other kernels, and every
  * other instance's whole step, run on the instances' streams.  The launch

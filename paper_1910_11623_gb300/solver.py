@@ -244,8 +244,9 @@ class TrainGraph:
 class Group:
     """Independent instances (each a Solver on its own stream) trained
     together: one group step trains every instance (the fused BF16 ones of a
-    common kernel variant through one grouped forward and one grouped
-    backward launch, mode "grouped"; or every step on its own stream, mode
+    common kernel variant and at most two tiles per SM through one grouped
+    forward and one grouped backward launch, mode "grouped"; or every step on
+    its own stream, mode
     "streams"), capture() makes it one CUDA graph, autotune() splits the SMs
     between the instances (cached per set of shapes in a JSON file)."""
 
