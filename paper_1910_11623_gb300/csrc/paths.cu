@@ -239,28 +239,38 @@ __global__ void k_loss_reduce(const double* __restrict__ path_loss, int M,
                               const float* __restrict__ Y, float* __restrict__ loss_out,
                               float* __restrict__ y0_out, int* __restrict__ nonfinite,
                               const double* __restrict__ path_alpha, float* __restrict__ alpha_sum) {
-    __shared__ double sh[1024], sa[1024];
+    // strided sums per thread, a fixed butterfly per warp, then the warps'
+    // sums in order by warp 0 (the same additions on every call)
+    __shared__ double sh[32], sa[32];
     double acc = 0.0, acca = 0.0;
     for (int m = threadIdx.x; m < M; m += blockDim.x) {
         acc += path_loss[m];
         if (path_alpha) acca += path_alpha[m];
     }
-    sh[threadIdx.x] = acc;
-    sa[threadIdx.x] = acca;
-    __syncthreads();
-    for (int s = blockDim.x / 2; s > 0; s >>= 1) {
-        if (threadIdx.x < s) {
-            sh[threadIdx.x] += sh[threadIdx.x + s];
-            sa[threadIdx.x] += sa[threadIdx.x + s];
-        }
-        __syncthreads();
+    const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5;
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) {
+        acc += __shfl_xor_sync(0xffffffffu, acc, o);
+        acca += __shfl_xor_sync(0xffffffffu, acca, o);
     }
-    if (threadIdx.x == 0) {
-        const double L = sh[0];
-        if (loss_out) *loss_out = (float)L;
-        if (y0_out) *y0_out = Y[0];
-        if (path_alpha) *alpha_sum = (float)sa[0];
-        if (!isfinite(L) || !isfinite(Y[0])) *nonfinite = 1;
+    if (lane == 0) { sh[wid] = acc; sa[wid] = acca; }
+    __syncthreads();
+    if (wid == 0) {
+        const int nw = (int)(blockDim.x >> 5);
+        acc = lane < nw ? sh[lane] : 0.0;
+        acca = lane < nw ? sa[lane] : 0.0;
+#pragma unroll
+        for (int o = 16; o > 0; o >>= 1) {
+            acc += __shfl_xor_sync(0xffffffffu, acc, o);
+            acca += __shfl_xor_sync(0xffffffffu, acca, o);
+        }
+        if (lane == 0) {
+            const double L = acc;
+            if (loss_out) *loss_out = (float)L;
+            if (y0_out) *y0_out = Y[0];
+            if (path_alpha) *alpha_sum = (float)acca;
+            if (!isfinite(L) || !isfinite(Y[0])) *nonfinite = 1;
+        }
     }
 }
 

@@ -609,35 +609,58 @@ __global__ void k_colsum_reduce(const float* __restrict__ part, int splits, int 
     if (lane == 0) out[(size_t)c * ldo] = accumulate ? out[(size_t)c * ldo] + s : s;
 }
 
-// out[r * ld + off + c] = sum_z part[z][r][c] for c < nc.  A block takes 32
-// consecutive columns of one row: warp g sums the splits z = g, g + 8, ...
-// for its 32 columns (one column per lane, every load in flight at once), and
-// warp 0 adds the eight warps' sums in order (bit-reproducible).
-__global__ void __launch_bounds__(256) k_reduce_split(const float* __restrict__ part, int splits, int rows, int N,
-                                                      int nc, float* __restrict__ out, int ld, int off) {
-    __shared__ float red[8][33];
-    const int lane = threadIdx.x & 31, g = threadIdx.x >> 5;
-    const int cblocks = (nc + 31) / 32;
-    const int r = blockIdx.x / cblocks, c = (blockIdx.x % cblocks) * 32 + lane;
-    const size_t stride = (size_t)rows * N;
-    float s = 0.f;
-    if (r < rows && c < nc) {
-        const float* q = part + (size_t)r * N + c;
-        int z = g;
-        for (; z + 24 < splits; z += 32) {
-            const float a0 = __ldcs(q + (size_t)z * stride), a1 = __ldcs(q + (size_t)(z + 8) * stride);
-            const float a2 = __ldcs(q + (size_t)(z + 16) * stride), a3 = __ldcs(q + (size_t)(z + 24) * stride);
-            s += (a0 + a1) + (a2 + a3);
+// The tail of one weight-gradient contraction in one launch.  Blocks [0, nred)
+// reduce the split-K partials: out[r * ld + off + c] = sum_z part[z][r][c] for
+// c < nc, a block per 32 consecutive columns of one row, warp g summing the
+// splits z = g, g + 8, ... (one column per lane, every load in flight at once)
+// and warp 0 adding the eight warps' sums in order (bit-reproducible).  Each
+// later block sums, one warp per entry,
+// the column-sum partials of pair 0's A operand (cs_part, then cst_part) over
+// the splits, in k_colsum_reduce's order.
+__global__ void __launch_bounds__(256) k_wgrad_finish(const float* __restrict__ part, int splits, int rows, int N,
+                                                      int nc, float* __restrict__ out, int ld, int off, int nred,
+                                                      const float* __restrict__ cs_part, float* __restrict__ cs_out,
+                                                      int cs_ld, const float* __restrict__ cst_part,
+                                                      float* __restrict__ cst_out, int cst_ld) {
+    if ((int)blockIdx.x < nred) {
+        __shared__ float red[8][33];
+        const int lane = threadIdx.x & 31, g = threadIdx.x >> 5;
+        const int cblocks = (nc + 31) / 32;
+        const int r = blockIdx.x / cblocks, c = (blockIdx.x % cblocks) * 32 + lane;
+        const size_t stride = (size_t)rows * N;
+        float s = 0.f;
+        if (r < rows && c < nc) {
+            const float* q = part + (size_t)r * N + c;
+            int z = g;
+            for (; z + 24 < splits; z += 32) {
+                const float a0 = __ldcs(q + (size_t)z * stride), a1 = __ldcs(q + (size_t)(z + 8) * stride);
+                const float a2 = __ldcs(q + (size_t)(z + 16) * stride), a3 = __ldcs(q + (size_t)(z + 24) * stride);
+                s += (a0 + a1) + (a2 + a3);
+            }
+            for (; z < splits; z += 8) s += __ldcs(q + (size_t)z * stride);
         }
-        for (; z < splits; z += 8) s += __ldcs(q + (size_t)z * stride);
-    }
-    red[g][lane] = s;
-    __syncthreads();
-    if (g == 0 && r < rows && c < nc) {
-        float t = red[0][lane];
+        red[g][lane] = s;
+        __syncthreads();
+        if (g == 0 && r < rows && c < nc) {
+            float t = red[0][lane];
 #pragma unroll
-        for (int k = 1; k < 8; ++k) t += red[k][lane];
-        out[(size_t)r * ld + off + c] = t;
+            for (int k = 1; k < 8; ++k) t += red[k][lane];
+            out[(size_t)r * ld + off + c] = t;
+        }
+        return;
+    }
+    const int e = ((int)blockIdx.x - nred) * 8 + (int)(threadIdx.x >> 5), lane = threadIdx.x & 31;
+    const bool second = e >= rows;
+    const int col = second ? e - rows : e;
+    const float* src = second ? cst_part : cs_part;
+    if (!src || col >= rows) return;
+    float s = 0.f;
+    for (int k = lane; k < splits; k += 32) s += src[(size_t)k * rows + col];
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) s += __shfl_xor_sync(0xffffffffu, s, o);
+    if (lane == 0) {
+        if (second) cst_out[(size_t)col * cst_ld] = s;
+        else cs_out[(size_t)col * cs_ld] = s;
     }
 }
 
@@ -722,19 +745,14 @@ static fbsde_status wgrad(fbsde_ctx* c, TcArgs a, int ncols_store, float* out, i
     double flops = 0;
     for (int q = 0; q < a.npairs; ++q) flops += 2.0 * a.rows * (double)ncols_store * P;
     FBSDE_TRY(tc_launch<true>(c, PROF_WGRAD, a, splits, EpiPartB{c->part, a.rows, a.N}, flops));
-    k_reduce_split<<<(unsigned)(a.rows * ((ncols_store + 31) / 32)), 256, 0, c->stream>>>(c->part, splits, a.rows, a.N,
-                                                                                   ncols_store, out, ld, off);
+    // the split-K reduction and the column sums in one launch
+    const int nred = a.rows * ((ncols_store + 31) / 32);
+    const int ncs = cs ? (a.rows * (cst_out ? 2 : 1) + 7) / 8 : 0;
+    k_wgrad_finish<<<(unsigned)(nred + ncs), 256, 0, c->stream>>>(
+        c->part, splits, a.rows, a.N, ncols_store, out, ld, off, nred, cs ? b->colpart : nullptr, cs_out, cs_ld,
+        cs && cst_out ? b->colpart + (size_t)splits * a.rows : nullptr, cst_out, cst_ld);
     FBSDE_CK_LAUNCH(c);
-    if (cs) {
-        k_colsum_reduce<<<nblk((size_t)a.rows * 32, 256), 256, 0, c->stream>>>(b->colpart, splits, a.rows, cs_out,
-                                                                              cs_ld, 0);
-        FBSDE_CK_LAUNCH(c);
-        if (cst_out) {
-            k_colsum_reduce<<<nblk((size_t)a.rows * 32, 256), 256, 0, c->stream>>>(
-                b->colpart + (size_t)splits * a.rows, splits, a.rows, cst_out, cst_ld, 0);
-            FBSDE_CK_LAUNCH(c);
-        }
-    } else if (cs_out) {
+    if (!cs && cs_out) {
         // the partial sums do not fit the scratch: a separate pass over pair 0's A
         return set_err(c, FBSDE_ERR_UNSUPPORTED, "column-sum scratch too small for this split");
     }
