@@ -1007,6 +1007,20 @@ __device__ __forceinline__ void bwdp_body(const BwdArgs& a, const int cta, const
                     st_tile16_packed(tile_h, row, c0, out);
                 }
                 slab_release(&B->slab[s], lane);
+                if (c0 < a.w) {
+                    // this slab's act' and S lines are dead once read (the next tile
+                    // rewrites them): drop them from L2 without a write-back.  Per
+                    // block, the warp's 32 rows of the two 8-column groups are eight
+                    // 128-byte lines; lanes 0-7 take the act' block's, 8-15 the S block's.
+                    __syncwarp();
+                    if (lane < 16) {
+                        const uint32_t* base = lane < 8 ? d1src : Ssrc;
+                        const size_t grp = (size_t)(c0 >> 3) + ((lane >> 2) & 1);
+                        const uint8_t* line =
+                            reinterpret_cast<const uint8_t*>(base + (grp * 128 + (size_t)lg * 32) * 4) + (lane & 3) * 128;
+                        asm volatile("discard.global.L2 [%0], 128;" ::"l"(line) : "memory");
+                    }
+                }
             }
             return true;
         };
