@@ -959,6 +959,16 @@ __device__ __forceinline__ void bwdp_body(const BwdArgs& a, const int cta, const
                 }
                 if (RES && top) tc::tmem_wait_st();
                 slab_release(&B->slab[s], lane);
+                if (!top && c0 < a.w) {
+                    // this slab's g_l lines are dead once read: drop them from L2
+                    __syncwarp();
+                    if (lane < 8) {
+                        const size_t grp = (size_t)(c0 >> 3) + ((lane >> 2) & 1);
+                        const uint8_t* line =
+                            reinterpret_cast<const uint8_t*>(gin + (grp * 128 + (size_t)lg * 32) * 4) + (lane & 3) * 128;
+                        asm volatile("discard.global.L2 [%0], 128;" ::"l"(line) : "memory");
+                    }
+                }
             }
             return true;
         };
