@@ -635,6 +635,15 @@ __global__ void __launch_bounds__(kPThreads, 1)
 // L+1..2L the adjoint through layer 2L+1-q (buffer q % 2).  Every phase
 // writes the operand tiles: h_l (tile_h) and h'_l (tile_d) in the up-sweep,
 // abar (tile_h) in the adjoint sweep.
+//
+// An up-sweep contraction fills both TMEM buffers, so it cannot run into the
+// other buffer while the previous epilogue works: it starts once every
+// epilogue warp has read its accumulator columns (barrier `tread`), each K
+// slice waiting for its slab of the operand tiles.  The top phase also sums
+// alpha h_L + h'_L over the tile's rows (the read-out gradient) into per-tile
+// partials.  The derivative scratch (act'(a_l), S_l) and the g_l blocks are
+// dropped from L2 once read (`discard.global.L2`), so dead scratch is never
+// written back to HBM.
 struct PipeBwdPlan {
     const BwdArgs* a;
     __device__ int nq() const { return 2 * a->L + 1; }
