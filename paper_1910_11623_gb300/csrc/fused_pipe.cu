@@ -716,6 +716,14 @@ __device__ __forceinline__ void bwdp_body(const BwdArgs& a, const int cta, const
                         const size_t blk = (size_t)(a.w / 2) * 128;
                         tc::prefetch_l2_bulk(a.G + (size_t)q * a.G_words + (size_t)t * blk, (uint32_t)(blk * 4));
                     }
+                    if (q > L) {
+                        // into L2 about one phase ahead of the adjoint epilogue of phase
+                        // q: this CTA's act' and S blocks of layer 2L - q
+                        const size_t blk = (size_t)(a.w / 2) * 128;
+                        const uint32_t* d1b = a.scratch + ((size_t)cta * 2 * L + (2 * L - q)) * blk;
+                        tc::prefetch_l2_bulk(d1b, (uint32_t)(blk * 4));
+                        tc::prefetch_l2_bulk(d1b + (size_t)L * blk, (uint32_t)(blk * 4));
+                    }
                     const CUtensorMap* m = plan.map(q);
                     const uint32_t bytes = (uint32_t)a.w * 128u;
                     for (int kc = 0; kc < plan.nk(q); ++kc, ++it) {
