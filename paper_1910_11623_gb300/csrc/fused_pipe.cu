@@ -222,14 +222,6 @@ __device__ __forceinline__ float warp_colsum8(const float (&v)[8], int lane) {
     return c;
 }
 
-// 16 columns (8 packed bf16x2 words) of `row` into a column-pair-major block
-// with an L2 eviction policy.
-__device__ __forceinline__ void st_pm16h_packed(uint32_t* blk, int row, int c0, const uint32_t (&u)[8], uint64_t pol) {
-    uint32_t* q = blk + (c0 >> 1) * 128 + row;
-#pragma unroll
-    for (int k = 0; k < 8; ++k) tc::st_global_hint(q + k * 128, u[k], pol);
-}
-
 // ---------------------------------------------------------------- forward + Z
 
 // Phase q of a tile: 0 lift, 1..L layers, L+1..2L reverse through layer
