@@ -65,3 +65,15 @@ def test_algorithmic_bytes_of_the_pipelined_kernels(bench):
     assert bench.fused_algorithmic_bytes(wn) == pytest.approx((fwdn + bwdn) / 2)
     # outside the fused kernels' limits there is no such figure
     assert bench.fused_algorithmic_bytes(w.with_prec("fp32")) is None
+
+
+def test_traffic_figure_only_for_the_sources_it_was_taken_on(bench, monkeypatch):
+    wl = "bsb_d100_n64_m4096_resnet5x256_tanh"
+    got = bench.ncu_traffic("bf16", wl)
+    # the committed figure is keyed to the current kernel sources
+    assert got is not None and got > 0
+    # any change to those sources withdraws it
+    monkeypatch.setattr(bench, "source_hash", lambda files=bench.KERNEL_SOURCES: "0" * 16)
+    assert bench.ncu_traffic("bf16", wl) is None
+    # and no figure exists for a workload never captured
+    assert bench.ncu_traffic("bf16", "no_such_workload") is None
